@@ -1,0 +1,155 @@
+/*
+ * gf2.h -- C ABI of the GB300 (sm_103a) GF(2) elimination library.
+ *
+ * Dense matrices over GF(2) (Albrecht & Pernet, "Efficient Decomposition of
+ * Dense Matrices over GF(2)"): PLS decomposition with rank (Proposition "PLS
+ * decomposition", Sec. 2; Algorithms MMPF, Sec. 4.1, and PLS, Sec. 5), the
+ * reduced row echelon form (Definition "Reduced Row Echelon Form", Sec. 2;
+ * computed from PLS as in the "PLS" column of Table 1, Sec. 7), the rank, and
+ * the product C = C + A.B used as the trailing update (Algorithm PLS, Sec. 5).
+ *
+ * MATRIX LAYOUT (all entry points). A matrix is (data, m, n, stride):
+ *   data   -- DEVICE pointer, 128-byte aligned, owned by the caller;
+ *   m, n   -- rows and columns (bits), 0 <= m, n < 2^31;
+ *   stride -- row pitch in 64-bit words, a multiple of 16 (128 bytes) and
+ *             >= ceil(n / 64).
+ * Row i occupies data[i*stride .. i*stride + stride). Column j of row i is bit
+ * (j & 63) of word data[i*stride + (j >> 6)]: least significant bit = leftmost
+ * column. Bits at columns >= n ("padding") are ignored on input and zero on
+ * output. Words past ceil(n/64) in a row are never read or written.
+ *
+ * PERMUTATIONS. P (length m) and Q (length n) are DEVICE int64 arrays holding
+ * swap vectors, as written by the Gaussian PLS algorithm (appendix): for
+ * i = 0 .. r-1, row i was swapped with row P[i] (P[i] >= i) and Q[i] is the
+ * column of the i-th pivot (strictly increasing). P[i] = i for i >= r and
+ * Q[i] = i for i >= r. A = P.L.S is recovered by applying the transpositions
+ * i <-> P[i] for i = r-1 down to 0 to the rows of L.S.
+ *
+ * ASYNCHRONY. Every call enqueues work on `stream` (a cudaStream_t, NULL = the
+ * legacy default stream) and returns without synchronising; results (rank
+ * included) are in device memory when the stream reaches that point. Host
+ * arguments are validated before anything is enqueued.
+ *
+ * WORKSPACE. Calls that take (work, work_bytes) need at least
+ * gf2_workspace_bytes(op, m, n, opts) bytes of DEVICE memory, 256-byte
+ * aligned, owned by the caller and not used by anything else until the stream
+ * has finished the call. work == NULL makes the library use a workspace it
+ * allocates (cudaMalloc) and keeps per device; calls that share that internal
+ * workspace must then be ordered on one stream.
+ *
+ * ERRORS. Every entry point returns 0 (GF2_OK) or a GF2_E* code and never
+ * throws. A non-zero return means nothing was enqueued (except GF2_ECUDA from
+ * a failed launch, after which the stream's work is undefined).
+ */
+#ifndef GF2_H
+#define GF2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GF2_OK 0
+#define GF2_EINVAL 1   /* null pointer, negative or too large size, stride < ceil(n/64), bad opts */
+#define GF2_EALIGN 2   /* data not 128-byte aligned, stride not a multiple of 16, work not 256-byte aligned */
+#define GF2_ENOMEM 3   /* internal workspace allocation failed */
+#define GF2_ECUDA 4    /* a CUDA runtime call failed (see gf2_last_cuda_error) */
+#define GF2_ENOSPACE 5 /* work_bytes smaller than gf2_workspace_bytes() */
+#define GF2_EDIM 6     /* mismatched dimensions (gf2_mul) */
+
+/* op codes for gf2_workspace_bytes */
+#define GF2_OP_PLS 1
+#define GF2_OP_RREF 2
+#define GF2_OP_RANK 3
+#define GF2_OP_MUL 4
+
+/* trailing-product form for gf2_mul and the recursive PLS */
+#define GF2_PRODUCT_AUTO 0
+#define GF2_PRODUCT_XOR 1    /* Gray-code XOR tables (Method of the Four Russians) */
+#define GF2_PRODUCT_TENSOR 2 /* 0/1 operands on the tensor cores, exact, low bit kept */
+
+/*
+ * Tuning knobs. None of them changes any result (rank, P, Q, L, S and RREF
+ * are unique for the pivot rule, whatever the blocking). Pass NULL for the
+ * defaults; a field left 0 means "choose automatically".
+ */
+typedef struct gf2_opts {
+    int k;              /* bits per Gray-code table (Sec. 3.1); only 8 is built, 0 = 8 */
+    int tile_words;     /* column tile of a table sweep, in words: 0, 4 or 8 */
+    int grid_ctas;      /* CTAs of a table sweep; 0 = one per SM */
+    int product;        /* GF2_PRODUCT_*; used by gf2_mul */
+    int64_t cutoff_cols;/* recursive PLS: MMPF base case at or below this many columns (Sec. 6); 0 = MMPF only */
+    int reserved[8];    /* must be zero */
+} gf2_opts;
+
+/*
+ * Bytes of workspace an operation needs for an m x n matrix (for GF2_OP_MUL,
+ * m x n is the shape of C and the inner dimension does not matter). Returns 0
+ * for invalid sizes.
+ */
+size_t gf2_workspace_bytes(int op, int64_t m, int64_t n, const gf2_opts *opts);
+
+/*
+ * PLS decomposition with rank, in place (Proposition "PLS decomposition";
+ * computed by block elimination over 64-column panels following MMPF,
+ * Sec. 4.1: pivot search, Gray-code tables of the pivot rows, table-driven row
+ * additions that write the multipliers of L, and the final compression of L).
+ *
+ * On return (stream-ordered): A holds L strictly below the diagonal in
+ * columns [0, r) (unit diagonal implied) and S in rows [0, r): row i < r is
+ * [L_i in cols < i | 1 at col i | 0 up to col Q[i] | S_i right of Q[i] in its
+ * original columns]; rows >= r hold only L. *rank = r. P, Q as above.
+ * Identical, bit for bit, to the Gaussian PLS algorithm of the appendix.
+ *   A      -- device, m x n, stride words per row (layout above), in/out;
+ *   P, Q   -- device int64, length m and n, out (may not alias A or work);
+ *   rank   -- device int64, out.
+ * m == 0 or n == 0 returns GF2_OK with rank 0 and identity P, Q.
+ */
+int gf2_pls(uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *P, int64_t *Q, int64_t *rank,
+            void *work, size_t work_bytes, const gf2_opts *opts, void *stream);
+
+/*
+ * Reduced row echelon form, in place (Definition "Reduced Row Echelon Form";
+ * the PLS route of Table 1: PLS decomposition, then R = (S restricted to its
+ * pivot columns)^-1 . S by an upper-triangular solve over 64-pivot blocks).
+ * On return rows [0, r) of A hold the RREF and rows [r, m) are zero.
+ *   pivots -- device int64, length n, nullable: pivots[i] = column of the
+ *             leading 1 of row i for i < r (the column rank profile), i for i >= r;
+ *   rank   -- device int64, out.
+ */
+int gf2_rref(uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *rank, int64_t *pivots,
+             void *work, size_t work_bytes, const gf2_opts *opts, void *stream);
+
+/*
+ * Rank only (the return value of the PLS algorithms). A is NOT modified: the
+ * elimination runs on a copy inside the workspace.
+ */
+int gf2_rank(const uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *rank, void *work,
+             size_t work_bytes, const gf2_opts *opts, void *stream);
+
+/*
+ * Product over GF(2): C = A.B (accumulate == 0) or C = C + A.B (accumulate
+ * != 0), the trailing update A_SE <- A_SE + A_SW.A_NE of Algorithm PLS
+ * (Sec. 5). A is m x k, B is k x n, C is m x n, each with its own stride.
+ * C must not overlap A or B. opts->product picks the XOR-table form or the
+ * tensor-core form (bit-exact in both).
+ */
+int gf2_mul(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64_t *B, int64_t sb,
+            int64_t m, int64_t k, int64_t n, int accumulate, void *work, size_t work_bytes,
+            const gf2_opts *opts, void *stream);
+
+/* Human-readable text for a GF2_* code (static storage). */
+const char *gf2_strerror(int code);
+
+/* cudaError_t value of the last CUDA failure seen by this thread (0 if none). */
+int gf2_last_cuda_error(void);
+
+/* Library version: major*10000 + minor*100 + patch. */
+int gf2_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GF2_H */

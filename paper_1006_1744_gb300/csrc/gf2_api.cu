@@ -1,0 +1,335 @@
+// gf2_api.cu -- C ABI entry points: argument checks, workspace, dispatch.
+#include <mutex>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "gf2_common.cuh"
+
+namespace gf2 {
+
+static thread_local int g_last_cuda = 0;
+
+int note_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return GF2_OK;
+    g_last_cuda = (int)e;
+    return GF2_ECUDA;
+}
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return 148;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+        return 148;
+    return n;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int64_t min_stride(int64_t n)
+{
+    int64_t s = ((n + 63) / 64 + 15) / 16 * 16;
+    return s < 16 ? 16 : s;
+}
+
+ElimLayout elim_layout(int op, int64_t m, int64_t n)
+{
+    ElimLayout L{};
+    const int64_t W = (n + 63) / 64;
+    const int64_t stride = min_stride(n);
+    size_t off = 0;
+    L.state = off;
+    off = align_up(off + sizeof(PanelState), 256);
+    L.perm = off;
+    off = align_up(off + (size_t)m * sizeof(int), 256);
+    L.side = off;
+    off = align_up(off + (size_t)2 * m * sizeof(u64), 256);
+    L.pmask = off;
+    off = align_up(off + (size_t)(W + 1) * sizeof(u64), 256);
+    L.out = off;
+    off = align_up(off + (size_t)m * stride * sizeof(u64), 256);
+    // Q (rref) or P,Q scratch (rank) share one area after `out`
+    L.rref_b = L.rref_x = L.rref_d = off;
+    if (op == GF2_OP_RREF) {
+        L.rref_b = off;
+        off = align_up(off + (size_t)m * W * sizeof(u64), 256);
+        L.rref_x = off;
+        off = align_up(off + (size_t)m * W * sizeof(u64), 256);
+        L.rref_d = off;
+        off = align_up(off + (size_t)((m + 63) / 64 + 1) * 64 * sizeof(u64), 256);
+    }
+    // int64 Q scratch for rref (length n)
+    off = align_up(off + (size_t)(n + 1) * sizeof(int64_t), 256);
+    L.total = off;
+    return L;
+}
+
+static size_t q_scratch_offset(const ElimLayout &L, int64_t n)
+{
+    return L.total - align_up((size_t)(n + 1) * sizeof(int64_t), 256);
+}
+
+int identity_fill(int64_t *P, int64_t m, int64_t *Q, int64_t n, int64_t *rank, cudaStream_t s);
+
+// internal workspace, one per device, grown on demand
+struct InternalWork {
+    std::mutex mu;
+    void *ptr[64] = {};
+    size_t bytes[64] = {};
+};
+static InternalWork g_work;
+
+static int get_work(void *&work, size_t &work_bytes, size_t need)
+{
+    if (work) {
+        if ((uintptr_t)work % 256)
+            return GF2_EALIGN;
+        if (work_bytes < need)
+            return GF2_ENOSPACE;
+        return GF2_OK;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return note_cuda(e);
+    if (dev < 0 || dev >= 64)
+        return GF2_EINVAL;
+    std::lock_guard<std::mutex> lock(g_work.mu);
+    if (g_work.bytes[dev] < need) {
+        if (g_work.ptr[dev]) {
+            cudaDeviceSynchronize();
+            cudaFree(g_work.ptr[dev]);
+            g_work.ptr[dev] = nullptr;
+            g_work.bytes[dev] = 0;
+        }
+        void *p = nullptr;
+        e = cudaMalloc(&p, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return GF2_ENOMEM;
+        }
+        g_work.ptr[dev] = p;
+        g_work.bytes[dev] = need;
+    }
+    work = g_work.ptr[dev];
+    work_bytes = g_work.bytes[dev];
+    return GF2_OK;
+}
+
+static int check_mat(const void *A, int64_t m, int64_t n, int64_t stride)
+{
+    if (m < 0 || n < 0 || m > INT32_MAX - 64 || n > INT32_MAX - 64)
+        return GF2_EINVAL;
+    const int64_t W = (n + 63) / 64;
+    if (stride < W || stride < 0)
+        return GF2_EINVAL;
+    if (m > 0 && n > 0) {
+        if (!A)
+            return GF2_EINVAL;
+        if ((uintptr_t)A % 128)
+            return GF2_EALIGN;
+        if (stride % 16)
+            return GF2_EALIGN;
+    }
+    return GF2_OK;
+}
+
+static int check_opts(const gf2_opts *o)
+{
+    if (!o)
+        return GF2_OK;
+    if (o->k != 0 && o->k != 8)
+        return GF2_EINVAL;
+    if (o->tile_words != 0 && o->tile_words != 4 && o->tile_words != 8)
+        return GF2_EINVAL;
+    if (o->grid_ctas < 0 || o->product < 0 || o->product > 2 || o->cutoff_cols < 0)
+        return GF2_EINVAL;
+    for (int i = 0; i < 8; ++i)
+        if (o->reserved[i])
+            return GF2_EINVAL;
+    return GF2_OK;
+}
+
+static Elim make_elim(uint64_t *A, int64_t m, int64_t n, int64_t stride, char *work, const ElimLayout &L,
+                      int64_t *P, int64_t *Q, bool with_out, const gf2_opts *o, cudaStream_t s)
+{
+    Elim e{};
+    e.A = A;
+    e.m = m;
+    e.n = n;
+    e.stride = stride;
+    e.W = (n + 63) / 64;
+    e.st = reinterpret_cast<PanelState *>(work + L.state);
+    e.perm = reinterpret_cast<int *>(work + L.perm);
+    e.side = reinterpret_cast<u64 *>(work + L.side);
+    e.pmask = reinterpret_cast<u64 *>(work + L.pmask);
+    e.out = with_out ? reinterpret_cast<uint64_t *>(work + L.out) : nullptr;
+    e.ostride = min_stride(n);
+    e.P = P;
+    e.Q = Q;
+    e.s = s;
+    e.tile_words = (o && o->tile_words) ? o->tile_words : 8;
+    e.grid = (o && o->grid_ctas) ? o->grid_ctas : sm_count();
+    return e;
+}
+
+}  // namespace gf2
+
+using namespace gf2;
+
+extern "C" {
+
+size_t gf2_workspace_bytes(int op, int64_t m, int64_t n, const gf2_opts *opts)
+{
+    if (check_opts(opts) || m < 0 || n < 0 || m > INT32_MAX - 64 || n > INT32_MAX - 64)
+        return 0;
+    switch (op) {
+    case GF2_OP_PLS:
+    case GF2_OP_RREF:
+    case GF2_OP_RANK:
+        return elim_layout(op, m, n).total;
+    case GF2_OP_MUL:
+        return align_up(mul_tensor_workspace(m, 0, n) + 256, 256);
+    default:
+        return 0;
+    }
+}
+
+int gf2_pls(uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *P, int64_t *Q, int64_t *rank,
+            void *work, size_t work_bytes, const gf2_opts *opts, void *stream)
+{
+    int rc = check_mat(A, m, n, stride);
+    if (rc)
+        return rc;
+    if ((rc = check_opts(opts)))
+        return rc;
+    if (!rank || (m > 0 && !P) || (n > 0 && !Q))
+        return GF2_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (m == 0 || n == 0)
+        return identity_fill(P, m, Q, n, rank, s);
+    const ElimLayout L = elim_layout(GF2_OP_PLS, m, n);
+    if ((rc = get_work(work, work_bytes, L.total)))
+        return rc;
+    Elim e = make_elim(A, m, n, stride, (char *)work, L, P, Q, true, opts, s);
+    if ((rc = elim_run(e)))
+        return rc;
+    if ((rc = elim_gather(e, rank)))
+        return rc;
+    return pls_finish(e);
+}
+
+int gf2_rref(uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *rank, int64_t *pivots, void *work,
+             size_t work_bytes, const gf2_opts *opts, void *stream)
+{
+    int rc = check_mat(A, m, n, stride);
+    if (rc)
+        return rc;
+    if ((rc = check_opts(opts)))
+        return rc;
+    if (!rank)
+        return GF2_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (m == 0 || n == 0)
+        return identity_fill(nullptr, 0, pivots, pivots ? n : 0, rank, s);
+    const ElimLayout L = elim_layout(GF2_OP_RREF, m, n);
+    if ((rc = get_work(work, work_bytes, L.total)))
+        return rc;
+    char *w = (char *)work;
+    int64_t *Qs = reinterpret_cast<int64_t *>(w + q_scratch_offset(L, n));
+    Elim e = make_elim(A, m, n, stride, w, L, nullptr, Qs, true, opts, s);
+    if ((rc = elim_run(e)))
+        return rc;
+    return rref_finish(e, L, w, rank, pivots);
+}
+
+int gf2_rank(const uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *rank, void *work,
+             size_t work_bytes, const gf2_opts *opts, void *stream)
+{
+    int rc = check_mat(A, m, n, stride);
+    if (rc)
+        return rc;
+    if ((rc = check_opts(opts)))
+        return rc;
+    if (!rank)
+        return GF2_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (m == 0 || n == 0)
+        return identity_fill(nullptr, 0, nullptr, 0, rank, s);
+    const ElimLayout L = elim_layout(GF2_OP_RANK, m, n);
+    if ((rc = get_work(work, work_bytes, L.total)))
+        return rc;
+    char *w = (char *)work;
+    uint64_t *copy = reinterpret_cast<uint64_t *>(w + L.out);
+    const int64_t cs = min_stride(n);
+    cudaError_t err = cudaMemcpy2DAsync(copy, (size_t)cs * 8, A, (size_t)stride * 8, (size_t)((n + 63) / 64) * 8,
+                                        (size_t)m, cudaMemcpyDeviceToDevice, s);
+    if (err != cudaSuccess)
+        return note_cuda(err);
+    Elim e = make_elim(copy, m, n, cs, w, L, nullptr, nullptr, false, opts, s);
+    if ((rc = elim_run(e)))
+        return rc;
+    return elim_gather(e, rank);
+}
+
+int gf2_mul(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64_t *B, int64_t sb, int64_t m,
+            int64_t k, int64_t n, int accumulate, void *work, size_t work_bytes, const gf2_opts *opts, void *stream)
+{
+    int rc;
+    if ((rc = check_mat(C, m, n, sc)) || (rc = check_mat(A, m, k, sa)) || (rc = check_mat(B, k, n, sb)))
+        return rc;
+    if ((rc = check_opts(opts)))
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (m == 0 || n == 0)
+        return GF2_OK;
+    if (!C)
+        return GF2_EINVAL;
+    const int product = opts ? opts->product : GF2_PRODUCT_AUTO;
+    if (product == GF2_PRODUCT_TENSOR) {
+        const size_t need = mul_tensor_workspace(m, k, n);
+        if ((rc = get_work(work, work_bytes, need)))
+            return rc;
+        return mul_tensor(C, sc, A, sa, B, sb, m, k, n, accumulate, work, work_bytes, s);
+    }
+    if (k == 0) {
+        if (!accumulate) {
+            cudaError_t err = cudaMemset2DAsync(C, (size_t)sc * 8, 0, (size_t)((n + 63) / 64) * 8, (size_t)m, s);
+            return note_cuda(err);
+        }
+        return GF2_OK;
+    }
+    return mul_xor(C, sc, A, sa, B, sb, m, k, n, accumulate, opts ? opts->tile_words : 0,
+                   opts ? opts->grid_ctas : 0, s);
+}
+
+const char *gf2_strerror(int code)
+{
+    switch (code) {
+    case GF2_OK:
+        return "ok";
+    case GF2_EINVAL:
+        return "invalid argument (null pointer, size, stride or option)";
+    case GF2_EALIGN:
+        return "misaligned data (128 bytes), stride (16 words) or workspace (256 bytes)";
+    case GF2_ENOMEM:
+        return "device memory allocation for the internal workspace failed";
+    case GF2_ECUDA:
+        return "CUDA runtime error (see gf2_last_cuda_error)";
+    case GF2_ENOSPACE:
+        return "workspace smaller than gf2_workspace_bytes()";
+    case GF2_EDIM:
+        return "mismatched dimensions";
+    default:
+        return "unknown error";
+    }
+}
+
+int gf2_last_cuda_error(void) { return g_last_cuda; }
+
+int gf2_version(void) { return 100; }
+
+}  // extern "C"

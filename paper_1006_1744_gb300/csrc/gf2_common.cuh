@@ -1,0 +1,134 @@
+// gf2_common.cuh -- shared internals of the GF(2) CUDA library (sm_103a).
+//
+// Bit layout (see include/gf2.h): column j of a row is bit (j & 63) of word
+// j >> 6, least significant bit = leftmost column.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gf2.h"
+
+typedef unsigned long long u64;
+
+#define GF2_FULL 0xffffffffu
+
+// ---------------------------------------------------------------------------
+// Per-call device state of the panel elimination (lives in the workspace).
+// The pivot kernel of panel b writes it, the table sweep of panel b reads it.
+// ---------------------------------------------------------------------------
+struct PanelState {
+    int r_cur;      // rank before the current panel
+    int r_next;     // rank after the current panel
+    int kbar;       // pivots found in the current panel (0..64)
+    int status;     // sticky device-side error code (0 = ok)
+    int zero_tail;  // 1 once every remaining row is zero in every remaining column
+    int pad0[3];
+    u64 J;          // pivot columns of the panel, as a bit mask of the panel word
+    int prow[64];   // physical row of pivot t (rows are never moved during elimination)
+    int pcol[64];   // panel-relative column of pivot t
+    u64 zmap[64];   // column c of the panel -> O-coordinates of the reduced basis row with a 1 at c
+    u64 xmap[64];   // column c -> multipliers of L (scattered to pivot columns) of that basis row
+    u64 zpiv[64];   // pivot t -> O-coordinates of its fully reduced row U_t
+    u64 newblk[64]; // pivot t -> its final panel word (U_t plus its own multipliers)
+};
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ u64 lowmask(int k)  // bits [0, k), k in [0, 64]
+{
+    return k >= 64 ? ~0ull : ((1ull << k) - 1ull);
+}
+
+__device__ __forceinline__ int ctz64(u64 x) { return __ffsll((long long)x) - 1; }
+
+// Software parallel bit extract: the bits of x at the set positions of m,
+// packed towards bit 0 (walks the runs of consecutive ones in m).
+__device__ __forceinline__ u64 pext64(u64 x, u64 m)
+{
+    u64 r = 0;
+    int k = 0;
+    while (m) {
+        int lo = ctz64(m);
+        u64 s = m >> lo;
+        int len = (~s == 0ull) ? 64 - lo : ctz64(~s);
+        u64 run = lowmask(len);
+        r |= ((x >> lo) & run) << k;
+        k += len;
+        m &= ~(run << lo);
+    }
+    return r;
+}
+
+// Software parallel bit deposit: the low bits of x placed at the set positions of m.
+__device__ __forceinline__ u64 pdep64(u64 x, u64 m)
+{
+    u64 r = 0;
+    int k = 0;
+    while (m) {
+        int lo = ctz64(m);
+        u64 s = m >> lo;
+        int len = (~s == 0ull) ? 64 - lo : ctz64(~s);
+        u64 run = lowmask(len);
+        r |= ((x >> k) & run) << lo;
+        k += len;
+        m &= ~(run << lo);
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+namespace gf2 {
+
+int note_cuda(cudaError_t e);  // records e for gf2_last_cuda_error, returns GF2_ECUDA or GF2_OK
+int sm_count();                // streaming multiprocessors of the current device
+size_t align_up(size_t x, size_t a);
+
+// Workspace carve-up of the panel elimination for an m x n matrix.
+struct ElimLayout {
+    size_t state;   // PanelState
+    size_t perm;    // int32[m]: position -> physical row
+    size_t side;    // u64[2][m]: panel word of each physical row (double buffered)
+    size_t pmask;   // u64[W]: pivot-column mask
+    size_t out;     // u64[m * stride]: rows in final order (pls / rref), or the copy (rank)
+    size_t rref_b;  // rref: non-pivot part of S, compacted
+    size_t rref_x;  // rref: solved non-pivot part
+    size_t rref_d;  // rref: inverses of the 64x64 diagonal blocks
+    size_t total;
+};
+int64_t min_stride(int64_t n);
+ElimLayout elim_layout(int op, int64_t m, int64_t n);
+
+struct Elim {
+    uint64_t *A;      // matrix being eliminated (caller's A, or the copy for rank)
+    int64_t m, n, stride, W;
+    PanelState *st;
+    int *perm;
+    u64 *side;
+    u64 *pmask;
+    uint64_t *out;    // final-order rows (nullptr for rank)
+    int64_t ostride;  // row pitch of out, words (minimal: ceil(n/64) rounded up to 16)
+    int64_t *P, *Q;   // nullable for rank
+    cudaStream_t s;
+    int tile_words, grid;
+};
+
+// panel elimination: runs every panel; afterwards st->r_next is the rank.
+int elim_run(const Elim &e);
+// writes P/Q identity fill, rank, gathers rows into e.out in final order
+int elim_gather(const Elim &e, int64_t *rank);
+// compress L in e.out and copy e.out back into e.A
+int pls_finish(const Elim &e);
+// RREF from the eliminated rows in e.out, written into e.A
+int rref_finish(const Elim &e, const ElimLayout &L, char *work, int64_t *rank, int64_t *pivots);
+// product
+int mul_xor(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64_t *B, int64_t sb,
+            int64_t m, int64_t k, int64_t n, int acc, int tile_words, int grid, cudaStream_t s);
+int mul_tensor(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64_t *B, int64_t sb,
+               int64_t m, int64_t k, int64_t n, int acc, void *work, size_t work_bytes, cudaStream_t s);
+size_t mul_tensor_workspace(int64_t m, int64_t k, int64_t n);
+
+}  // namespace gf2

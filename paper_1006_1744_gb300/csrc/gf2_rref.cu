@@ -1,0 +1,305 @@
+// gf2_rref.cu -- reduced row echelon form from the PLS elimination.
+//
+// The "PLS" column of Table 1 (Sec. 7) times a PLS decomposition followed by
+// the RREF computed from it; the paper does not spell out the second step. Here
+// it is the upper-triangular solve R = (S_J)^-1 . S, where S is the echelon
+// part of the pivot rows and S_J its columns at the pivot positions Q[0..r)
+// (unit upper triangular). With the columns split into pivot and non-pivot
+// ones, S = [U1 | B] and R = [I | U1^-1 B]; only X = U1^-1 B is computed
+// (back substitution over 64-pivot blocks, from the last block up), then R is
+// scattered back to the original column order. The RREF is unique
+// (Definition "Reduced Row Echelon Form"), so this matches any other route.
+#include "gf2_common.cuh"
+
+namespace {
+
+// Per pivot row i (< r): drop everything left of its pivot Q[i], split the
+// remaining bits into pivot columns (-> U1 row i, positions i.., stored in the
+// caller's matrix which is overwritten by the result anyway) and non-pivot
+// columns (-> B row i, positions Q[i]-i .., the positions before are zero).
+__global__ void k_rref_compact(const uint64_t *__restrict__ S, int64_t stride, const int64_t *__restrict__ Q,
+                               const u64 *__restrict__ pmask, const PanelState *__restrict__ st,
+                               uint64_t *__restrict__ U1, u64 *__restrict__ Bc, int64_t sb, int n, int W)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = st->r_next;
+    if (i >= r)
+        return;
+    const int nn = n - r;
+    const int64_t q = Q[i];
+    const uint64_t *row = S + (int64_t)i * stride;
+    uint64_t *urow = U1 + (int64_t)i * stride;
+    u64 *brow = Bc + (int64_t)i * sb;
+    // U1 stream from position i, B stream from position q - i
+    int64_t up = i, bp = q - i;
+    int64_t uw = up >> 6, bw = bp >> 6;
+    u64 ucur = 0, bcur = 0;
+    const int NBw = (nn + 63) >> 6;
+    for (int64_t w = 0; w < bw && w < NBw; ++w)
+        brow[w] = 0;
+    for (int64_t w = q >> 6; w < W; ++w) {
+        u64 word = row[w];
+        u64 valid = (w == W - 1 && (n & 63)) ? lowmask(n & 63) : ~0ull;
+        if (w == (q >> 6))
+            valid &= ~lowmask((int)(q & 63));
+        word &= valid;
+        const u64 pm = pmask[w] & valid, nm = ~pmask[w] & valid;
+        const u64 ub = pext64(word, pm), bb = pext64(word, nm);
+        const int uk = __popcll(pm), bk = __popcll(nm);
+        int off = (int)(up & 63);
+        ucur |= ub << off;
+        if (off + uk >= 64) {
+            urow[uw++] = ucur;
+            ucur = off == 0 ? 0ull : (ub >> (64 - off));
+        }
+        up += uk;
+        off = (int)(bp & 63);
+        bcur |= bb << off;
+        if (off + bk >= 64) {
+            brow[bw++] = bcur;
+            bcur = off == 0 ? 0ull : (bb >> (64 - off));
+        }
+        bp += bk;
+    }
+    if (up & 63)
+        urow[uw] = ucur;
+    if ((bp & 63) && bw < NBw)
+        brow[bw] = bcur;
+}
+
+// Inverses of the 64x64 unit upper-triangular diagonal blocks of U1 (one warp
+// per block; rows past the rank are identity). Back substitution by columns:
+// X = I; for h = 63 .. 0, every row i < h with D[i][h] = 1 gets X[h] added.
+__global__ void k_diag_inv(const uint64_t *__restrict__ U1, int64_t stride, const PanelState *__restrict__ st,
+                           u64 *__restrict__ Dinv, int nblk)
+{
+    const int lane = threadIdx.x & 31;
+    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int r = st->r_next;
+    if (q >= nblk || 64 * q >= r)
+        return;
+    const int base = 64 * q;
+    u64 d0 = 1ull << lane, d1 = 1ull << (lane + 32);
+    if (base + lane < r)
+        d0 |= U1[(int64_t)(base + lane) * stride + q] & ~lowmask(lane + 1);
+    if (base + lane + 32 < r)
+        d1 |= U1[(int64_t)(base + lane + 32) * stride + q] & ~lowmask(lane + 33);
+    u64 x0 = 1ull << lane, x1 = 1ull << (lane + 32);
+    for (int h = 63; h >= 1; --h) {
+        const u64 xh = __shfl_sync(GF2_FULL, h < 32 ? x0 : x1, h & 31);
+        if (lane < h && ((d0 >> h) & 1ull))
+            x0 ^= xh;
+        if (lane + 32 < h && ((d1 >> h) & 1ull))
+            x1 ^= xh;
+    }
+    Dinv[(int64_t)q * 64 + lane] = x0;
+    Dinv[(int64_t)q * 64 + lane + 32] = x1;
+}
+
+// Gray-code tables of 64 rows x TWB words: T[g][v][w] = sum of rows 8g+e (bit e of v).
+template <int TWB>
+__device__ __forceinline__ void build_tables(const u64 *__restrict__ rows, u64 *__restrict__ T, int tid)
+{
+    for (int e = tid; e < 8 * TWB * 16; e += blockDim.x) {
+        const int vh = e & 15, gw = e >> 4, wi = gw % TWB, g = gw / TWB;
+        const u64 *Og = rows + (8 * g) * TWB + wi;
+        u64 cur = 0;
+#pragma unroll
+        for (int bit = 0; bit < 4; ++bit)
+            if ((vh >> bit) & 1)
+                cur ^= Og[(4 + bit) * TWB];
+        u64 *Tg = T + (g * 256 + (vh << 4)) * TWB + wi;
+        Tg[0] = cur;
+#pragma unroll
+        for (int i = 1; i < 16; ++i) {
+            cur ^= Og[(__ffs(i) - 1) * TWB];
+            Tg[(i ^ (i >> 1)) * TWB] = cur;
+        }
+    }
+}
+
+// One 64-pivot block q of the back substitution X = U1^-1 B:
+//   X_q = Dinv_q . B_q            (B_q already holds every update from below)
+//   B_i += U1[i, block q] . X_q   for every row i above the block.
+constexpr int TWB = 2;
+__global__ void __launch_bounds__(256, 1)
+k_rref_step(u64 *__restrict__ Bc, u64 *__restrict__ Xc, int64_t sb, const uint64_t *__restrict__ U1,
+            int64_t stride, const u64 *__restrict__ Dinv, const PanelState *__restrict__ st, int n, int q)
+{
+    extern __shared__ __align__(16) u64 smr[];
+    u64 *sTB = smr;                  // [8][256][TWB]
+    u64 *sTX = sTB + 8 * 256 * TWB;  // [8][256][TWB]
+    u64 *sB = sTX + 8 * 256 * TWB;   // [64][TWB]
+    u64 *sX = sB + 64 * TWB;         // [64][TWB]
+    u64 *sD = sX + 64 * TWB;         // [64]
+    const int r = st->r_next;
+    const int nn = n - r;
+    const int NB = (nn + 63) >> 6;
+    const int base = 64 * q;
+    if (base >= r || NB == 0)
+        return;
+    const int tid = threadIdx.x;
+    const int nrow = min(64, r - base);
+    const int tiles = (NB + TWB - 1) / TWB;
+    const int above = base;
+    int chunks = gridDim.x / tiles;
+    if (chunks < 1)
+        chunks = 1;
+    int R = (above + chunks - 1) / chunks;
+    R = (R + 255) / 256 * 256;
+    if (R == 0)
+        R = 256;
+    chunks = above > 0 ? (above + R - 1) / R : 1;
+    const int items = tiles * chunks;
+    if (tid < 64)
+        sD[tid] = Dinv[(int64_t)q * 64 + tid];
+    int cur_tile = -1;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int tile = item / chunks, chunk = item % chunks;
+        const int wb = tile * TWB;
+        if (tile != cur_tile) {
+            __syncthreads();
+            for (int e = tid; e < 64 * TWB; e += blockDim.x) {
+                const int s = e / TWB, wi = e % TWB;
+                sB[e] = (s < nrow && wb + wi < NB) ? Bc[(int64_t)(base + s) * sb + wb + wi] : 0ull;
+            }
+            __syncthreads();
+            build_tables<TWB>(sB, sTB, tid);
+            __syncthreads();
+            for (int e = tid; e < 64 * TWB; e += blockDim.x) {
+                const int s = e / TWB, wi = e % TWB;
+                const u64 d = sD[s];
+                u64 acc = 0;
+#pragma unroll
+                for (int g = 0; g < 8; ++g)
+                    acc ^= sTB[(g * 256 + (int)((d >> (8 * g)) & 255ull)) * TWB + wi];
+                sX[e] = acc;
+                if (chunk == 0 && s < nrow && wb + wi < NB)
+                    Xc[(int64_t)(base + s) * sb + wb + wi] = acc;
+            }
+            __syncthreads();
+            build_tables<TWB>(sX, sTX, tid);
+            __syncthreads();
+            cur_tile = tile;
+        }
+        const int i0 = chunk * R, i1 = min(above, i0 + R);
+        for (int i = i0 + tid; i < i1; i += blockDim.x) {
+            const u64 u = U1[(int64_t)i * stride + q];
+            u64 a0 = 0, a1 = 0;
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                const ulonglong2 e2 =
+                    *reinterpret_cast<const ulonglong2 *>(sTX + (g * 256 + (int)((u >> (8 * g)) & 255ull)) * TWB);
+                a0 ^= e2.x;
+                a1 ^= e2.y;
+            }
+            u64 *brow = Bc + (int64_t)i * sb + wb;
+            brow[0] ^= a0;
+            if (wb + 1 < NB)
+                brow[1] ^= a1;
+        }
+    }
+}
+
+// R row i < r: 1 at Q[i], X row i deposited into the non-pivot columns.
+// Rows >= r: zero.
+__global__ void k_rref_scatter(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ Xc, int64_t sb,
+                               const int64_t *__restrict__ Q, const u64 *__restrict__ pmask,
+                               const PanelState *__restrict__ st, int m, int n, int W)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m)
+        return;
+    const int r = st->r_next;
+    uint64_t *row = A + (int64_t)i * stride;
+    if (i >= r) {
+        for (int w = 0; w < W; ++w)
+            row[w] = 0;
+        return;
+    }
+    const u64 *xr = Xc + (int64_t)i * sb;
+    const int64_t q = Q[i];
+    int64_t xp = 0;
+    for (int w = 0; w < W; ++w) {
+        const u64 valid = (w == W - 1 && (n & 63)) ? lowmask(n & 63) : ~0ull;
+        const u64 nm = ~pmask[w] & valid;
+        const int k = __popcll(nm);
+        u64 v = 0;
+        if (k) {
+            const int off = (int)(xp & 63);
+            u64 bits = xr[xp >> 6] >> off;
+            if (off + k > 64)
+                bits |= xr[(xp >> 6) + 1] << (64 - off);
+            v = pdep64(bits & lowmask(k), nm);
+            xp += k;
+        }
+        if ((q >> 6) == w)
+            v |= 1ull << (q & 63);
+        row[w] = v;
+    }
+}
+
+__global__ void k_rref_outputs(const int64_t *__restrict__ Q, const PanelState *__restrict__ st, int n,
+                               int64_t *__restrict__ pivots, int64_t *__restrict__ rank)
+{
+    const int r = st->r_next;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pivots)
+        for (int i = g; i < n; i += gridDim.x * blockDim.x)
+            pivots[i] = i < r ? Q[i] : i;
+    if (g == 0 && rank)
+        *rank = r;
+}
+
+__global__ void k_pmask2(const int64_t *__restrict__ Q, const PanelState *__restrict__ st, u64 *__restrict__ pmask)
+{
+    const int r = st->r_next;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < r; s += gridDim.x * blockDim.x) {
+        const int64_t c = Q[s];
+        atomicOr(&pmask[c >> 6], 1ull << (c & 63));
+    }
+}
+
+}  // namespace
+
+namespace gf2 {
+
+int rref_finish(const Elim &e, const ElimLayout &L, char *work, int64_t *rank, int64_t *pivots)
+{
+    const int m = (int)e.m, n = (int)e.n, W = (int)e.W;
+    const int64_t sb = e.W;  // row pitch of B and X in words
+    u64 *Bc = reinterpret_cast<u64 *>(work + L.rref_b);
+    u64 *Xc = reinterpret_cast<u64 *>(work + L.rref_x);
+    u64 *Dinv = reinterpret_cast<u64 *>(work + L.rref_d);
+    cudaError_t err = cudaMemsetAsync(e.pmask, 0, (size_t)W * sizeof(u64), e.s);
+    if (err != cudaSuccess)
+        return note_cuda(err);
+    k_pmask2<<<64, 256, 0, e.s>>>(e.Q, e.st, e.pmask);
+    const int rmax = m < n ? m : n;
+    k_rref_compact<<<(rmax + 127) / 128, 128, 0, e.s>>>(e.out, e.ostride, e.Q, e.pmask, e.st, e.A, Bc, sb, n, W);
+    const int nblk = (rmax + 63) / 64;
+    k_diag_inv<<<(nblk + 3) / 4, 128, 0, e.s>>>(e.A, e.stride, e.st, Dinv, nblk);
+    int rc = note_cuda(cudaGetLastError());
+    if (rc)
+        return rc;
+    const int grid = sm_count();
+    const size_t smem = (size_t)(2 * 8 * 256 * TWB + 2 * 64 * TWB + 64) * sizeof(u64);
+    static bool attr_set = false;
+    if (!attr_set) {
+        rc = note_cuda(cudaFuncSetAttribute(k_rref_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (rc)
+            return rc;
+        attr_set = true;
+    }
+    for (int q = nblk - 1; q >= 0; --q) {
+        k_rref_step<<<grid, 256, smem, e.s>>>(Bc, Xc, sb, e.A, e.stride, Dinv, e.st, n, q);
+        rc = note_cuda(cudaGetLastError());
+        if (rc)
+            return rc;
+    }
+    k_rref_scatter<<<(m + 127) / 128, 128, 0, e.s>>>(e.A, e.stride, Xc, sb, e.Q, e.pmask, e.st, m, n, W);
+    k_rref_outputs<<<32, 256, 0, e.s>>>(e.Q, e.st, n, pivots, rank);
+    return note_cuda(cudaGetLastError());
+}
+
+}  // namespace gf2

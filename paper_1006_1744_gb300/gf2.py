@@ -1,0 +1,180 @@
+"""Thin ctypes binding of the C ABI in ``include/gf2.h`` (argument marshalling only).
+
+Matrices are ``torch.int64`` CUDA tensors of shape (m, stride) holding the
+packed bits (column j = bit j&63 of word j>>6); the bit patterns are those of
+uint64. P, Q, rank and pivots are ``torch.int64`` CUDA tensors. Every call is
+asynchronous on ``stream`` (default: PyTorch's current stream) and raises
+``Gf2Error`` on a non-zero return code. There is no CPU fallback: a missing
+``libgf2.so`` raises immediately.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libgf2.so")
+_lock = threading.Lock()
+_lib = None
+
+OP_PLS, OP_RREF, OP_RANK, OP_MUL = 1, 2, 3, 4
+PRODUCT_AUTO, PRODUCT_XOR, PRODUCT_TENSOR = 0, 1, 2
+
+_i64 = ctypes.c_int64
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+_int = ctypes.c_int
+
+
+class Gf2Error(RuntimeError):
+    def __init__(self, code: int, what: str):
+        msg = lib().gf2_strerror(code).decode()
+        if code == 4:
+            msg += f" (cudaError {lib().gf2_last_cuda_error()})"
+        super().__init__(f"{what}: {msg} [code {code}]")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("k", _int), ("tile_words", _int), ("grid_ctas", _int), ("product", _int),
+                ("cutoff_cols", _i64), ("reserved", _int * 8)]
+
+
+SYMBOLS = {
+    "gf2_workspace_bytes": (_sz, [_int, _i64, _i64, _vp]),
+    "gf2_pls": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),
+    "gf2_rref": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _vp, _sz, _vp, _vp]),
+    "gf2_rank": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _sz, _vp, _vp]),
+    "gf2_mul": (_int, [_vp, _i64, _vp, _i64, _vp, _i64, _i64, _i64, _i64, _int, _vp, _sz, _vp, _vp]),
+    "gf2_strerror": (ctypes.c_char_p, [_int]),
+    "gf2_last_cuda_error": (_int, []),
+    "gf2_version": (_int, []),
+}
+
+
+def lib_path() -> str:
+    return _LIBPATH
+
+
+def lib():
+    """Load libgf2.so (built by ``paper_1006_1744_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIBPATH):
+                raise RuntimeError(f"{_LIBPATH} is missing: build it with `python -m paper_1006_1744_gb300.build` "
+                                   "(there is no CPU fallback)")
+            L = ctypes.CDLL(_LIBPATH)
+            for name, (res, args) in SYMBOLS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _opts(opts):
+    if opts is None:
+        return None
+    if isinstance(opts, Opts):
+        return ctypes.byref(opts)
+    o = Opts()
+    for k, v in dict(opts).items():
+        setattr(o, k, v)
+    return ctypes.byref(o)
+
+
+def _check(code, what):
+    if code != 0:
+        raise Gf2Error(code, what)
+
+
+def _mat(A, n, what):
+    if A.dtype != torch.int64 or A.dim() != 2 or not A.is_cuda:
+        raise ValueError(f"{what}: expected a 2-D torch.int64 CUDA tensor (packed rows)")
+    if A.stride(1) != 1:
+        raise ValueError(f"{what}: rows must be contiguous")
+    return A.shape[0], A.stride(0)
+
+
+def workspace_bytes(op: int, m: int, n: int, opts=None) -> int:
+    return int(lib().gf2_workspace_bytes(op, m, n, _opts(opts)))
+
+
+def new_workspace(op: int, m: int, n: int, device=None, opts=None) -> torch.Tensor:
+    nbytes = workspace_bytes(op, m, n, opts)
+    return torch.empty(max(nbytes, 256) // 8 + 32, dtype=torch.int64, device=device or "cuda")
+
+
+def _work(work):
+    if work is None:
+        return None, 0
+    base = work.data_ptr()
+    aligned = (base + 255) // 256 * 256
+    return aligned, work.numel() * 8 - (aligned - base)
+
+
+def pls(A: torch.Tensor, n: int, P=None, Q=None, rank=None, work=None, opts=None, stream=None):
+    """In-place PLS decomposition. Returns (P, Q, rank) device tensors."""
+    m, stride = _mat(A, n, "gf2_pls")
+    dev = A.device
+    P = torch.empty(max(m, 1), dtype=torch.int64, device=dev) if P is None else P
+    Q = torch.empty(max(n, 1), dtype=torch.int64, device=dev) if Q is None else Q
+    rank = torch.empty(1, dtype=torch.int64, device=dev) if rank is None else rank
+    wp, wb = _work(work)
+    _check(lib().gf2_pls(_ptr(A), m, n, stride, _ptr(P), _ptr(Q), _ptr(rank), wp, wb, _opts(opts),
+                         _stream(stream)), "gf2_pls")
+    return P[:m], Q[:n], rank
+
+
+def rref(A: torch.Tensor, n: int, rank=None, pivots=None, work=None, opts=None, stream=None,
+         want_pivots=True):
+    """In-place reduced row echelon form. Returns (rank, pivots) device tensors."""
+    m, stride = _mat(A, n, "gf2_rref")
+    dev = A.device
+    rank = torch.empty(1, dtype=torch.int64, device=dev) if rank is None else rank
+    if pivots is None and want_pivots:
+        pivots = torch.empty(max(n, 1), dtype=torch.int64, device=dev)
+    wp, wb = _work(work)
+    _check(lib().gf2_rref(_ptr(A), m, n, stride, _ptr(rank), _ptr(pivots), wp, wb, _opts(opts),
+                          _stream(stream)), "gf2_rref")
+    return rank, (pivots[:n] if pivots is not None else None)
+
+
+def rank(A: torch.Tensor, n: int, rank=None, work=None, opts=None, stream=None):
+    """Rank (A unchanged). Returns a device tensor of shape (1,)."""
+    m, stride = _mat(A, n, "gf2_rank")
+    rank = torch.empty(1, dtype=torch.int64, device=A.device) if rank is None else rank
+    wp, wb = _work(work)
+    _check(lib().gf2_rank(_ptr(A), m, n, stride, _ptr(rank), wp, wb, _opts(opts), _stream(stream)),
+           "gf2_rank")
+    return rank
+
+
+def mul(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, m: int, k: int, n: int, accumulate=False,
+        work=None, opts=None, stream=None):
+    """C = A.B (or C + A.B) over GF(2), in place in C."""
+    _, sc = _mat(C, n, "gf2_mul C")
+    _, sa = _mat(A, k, "gf2_mul A")
+    _, sb = _mat(B, n, "gf2_mul B")
+    wp, wb = _work(work)
+    _check(lib().gf2_mul(_ptr(C), sc, _ptr(A), sa, _ptr(B), sb, m, k, n, int(bool(accumulate)), wp, wb,
+                         _opts(opts), _stream(stream)), "gf2_mul")
+    return C

@@ -1,0 +1,99 @@
+"""The C-ABI library builds, loads and exports every declared symbol; host-side
+argument checks and workspace sizing answer without a GPU (no compute calls)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_1006_1744_gb300 import build
+    return build.build()
+
+
+def declared(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gf2_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_headers_declare_the_boundary():
+    names = declared("gf2.h")
+    for want in ("gf2_pls", "gf2_rref", "gf2_rank", "gf2_mul", "gf2_workspace_bytes", "gf2_strerror"):
+        assert want in names
+
+
+@pytest.mark.parametrize("header,lib", [("gf2.h", "libgf2.so"), ("gf2_synth.h", "libgf2synth.so")])
+def test_library_exports_every_declared_symbol(built, header, lib):
+    L = ctypes.CDLL(built[lib])
+    for name in declared(header):
+        assert hasattr(L, name), f"{lib} does not export {name}"
+
+
+def test_binding_covers_the_header(built):
+    from paper_1006_1744_gb300 import gf2
+    assert set(declared("gf2.h")) == set(gf2.SYMBOLS)
+    assert gf2.lib().gf2_version() >= 100
+    assert gf2.lib().gf2_strerror(0) == b"ok"
+    assert b"align" in gf2.lib().gf2_strerror(2)
+
+
+def test_workspace_bytes_host_only(built):
+    from paper_1006_1744_gb300 import gf2
+    small = gf2.workspace_bytes(gf2.OP_PLS, 64, 64)
+    big = gf2.workspace_bytes(gf2.OP_PLS, 16384, 16384)
+    assert 0 < small < big
+    assert big >= 16384 * 256 * 8  # at least one copy of the matrix (rows in final order)
+    assert gf2.workspace_bytes(gf2.OP_RREF, 1024, 1024) > gf2.workspace_bytes(gf2.OP_PLS, 1024, 1024)
+    assert gf2.workspace_bytes(gf2.OP_PLS, -1, 5) == 0
+    assert gf2.workspace_bytes(99, 5, 5) == 0
+    bad = gf2.Opts()
+    bad.k = 5
+    assert gf2.workspace_bytes(gf2.OP_PLS, 64, 64, bad) == 0
+
+
+def test_argument_checks_reject_before_any_device_work(built):
+    """Invalid arguments are refused on the host: nothing is dereferenced."""
+    from paper_1006_1744_gb300 import gf2
+    L = gf2.lib()
+    fake = 1 << 40          # 128-byte aligned, never touched
+    rank = 1 << 41
+    P, Q = 1 << 42, 1 << 43
+    EINVAL, EALIGN = 1, 2
+    assert L.gf2_pls(None, 8, 8, 16, P, Q, rank, None, 0, None, None) == EINVAL
+    assert L.gf2_pls(fake + 8, 8, 8, 16, P, Q, rank, None, 0, None, None) == EALIGN
+    assert L.gf2_pls(fake, 8, 8, 15, P, Q, rank, None, 0, None, None) == EALIGN
+    assert L.gf2_pls(fake, 8, 130, 2, P, Q, rank, None, 0, None, None) == EINVAL  # stride < ceil(n/64)
+    assert L.gf2_pls(fake, -1, 8, 16, P, Q, rank, None, 0, None, None) == EINVAL
+    assert L.gf2_pls(fake, 8, 8, 16, None, Q, rank, None, 0, None, None) == EINVAL
+    assert L.gf2_pls(fake, 8, 8, 16, P, Q, None, None, 0, None, None) == EINVAL
+    bad = gf2.Opts()
+    bad.tile_words = 3
+    assert L.gf2_pls(fake, 8, 8, 16, P, Q, rank, None, 0, ctypes.byref(bad), None) == EINVAL
+    bad = gf2.Opts()
+    bad.reserved[2] = 1
+    assert L.gf2_rref(fake, 8, 8, 16, rank, None, None, 0, ctypes.byref(bad), None) == EINVAL
+    assert L.gf2_rank(fake, 8, 8, 16, None, None, 0, None, None) == EINVAL
+    # misaligned or undersized caller workspace
+    assert L.gf2_pls(fake, 8, 8, 16, P, Q, rank, fake + 64, 1 << 30, None, None) == EALIGN
+    assert L.gf2_pls(fake, 8, 8, 16, P, Q, rank, fake, 16, None, None) == 5  # GF2_ENOSPACE
+    # product: bad strides
+    assert L.gf2_mul(fake, 16, fake, 16, fake, 7, 8, 8, 8, 0, None, 0, None, None) == EALIGN
+
+
+def test_product_path_refuses_without_library(tmp_path, monkeypatch):
+    """A missing build fails loudly instead of falling back to the CPU."""
+    import importlib
+    import paper_1006_1744_gb300.gf2 as g
+    mod = importlib.reload(g)
+    monkeypatch.setattr(mod, "_LIBPATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(mod, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        mod.lib()
+    importlib.reload(g)
