@@ -149,6 +149,24 @@ int gf2_last_cuda_error(void);
 /* Library version: major*10000 + minor*100 + patch. */
 int gf2_version(void);
 
+/*
+ * Diagnostics (not part of the method). flags: 1 = count every kernel launch
+ * of the library; 2 = also bracket each launch of the timed kernel classes
+ * with a pair of CUDA events on the launching stream. gf2_prof_collect() waits
+ * for the recorded events (host-blocking), adds their elapsed times to the
+ * class totals and returns the totals of class `cls` since gf2_prof_reset().
+ * Profiling state is process-wide; not for concurrent use from several threads.
+ */
+#define GF2_PROF_SWEEP 0 /* table sweep of a panel (MakeTable1 + AddRowsFromTable) */
+#define GF2_PROF_PIVOT 1 /* pivot search of a panel (PlsSubmatrix) */
+#define GF2_PROF_RREF 2  /* one 64-pivot block of the RREF back substitution */
+#define GF2_PROF_MUL 3   /* product kernels */
+#define GF2_PROF_CLASSES 4
+void gf2_prof_enable(int flags);
+void gf2_prof_reset(void);
+long long gf2_prof_launches(void);
+int gf2_prof_collect(int cls, double *ms_total, long long *launches);
+
 #ifdef __cplusplus
 }
 #endif

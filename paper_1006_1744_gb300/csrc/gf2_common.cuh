@@ -84,6 +84,9 @@ __device__ __forceinline__ u64 pdep64(u64 x, u64 m)
 namespace gf2 {
 
 int note_cuda(cudaError_t e);  // records e for gf2_last_cuda_error, returns GF2_ECUDA or GF2_OK
+void prof_launched(int count);              // counts kernel launches when profiling is on
+int prof_begin(cudaStream_t s);             // event before a timed launch (-1: profiling off)
+void prof_end(cudaStream_t s, int cls, int token);
 int sm_count();                // streaming multiprocessors of the current device
 size_t align_up(size_t x, size_t a);
 

@@ -132,7 +132,10 @@ int mul_xor(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64
         g = (int)items;
     if (g < 1)
         g = 1;
+    const int tok = prof_begin(s);
     k_mul_xor<TW, RPT><<<g, 256, smem, s>>>(C, sc, A, sa, B, sb, (int)m, (int)k, (int)n, acc);
+    prof_end(s, GF2_PROF_MUL, tok);
+    prof_launched(1);
     return note_cuda(cudaGetLastError());
 }
 

@@ -683,8 +683,11 @@ int launch_sweep(const gf2::Elim &e, int b)
     }
     const u64 *cur = e.side + (size_t)(b & 1) * e.m;
     u64 *nxt = e.side + (size_t)((b + 1) & 1) * e.m;
+    const int tok = gf2::prof_begin(e.s);
     k_sweep<TW, RPT, MINB><<<e.grid * MINB, 256, smem, e.s>>>(e.A, e.stride, cur, nxt, e.perm, e.st, e.out,
                                                               e.ostride, (int)e.m, (int)e.W, b);
+    gf2::prof_end(e.s, GF2_PROF_SWEEP, tok);
+    gf2::prof_launched(1);
     return gf2::note_cuda(cudaGetLastError());
 }
 
@@ -695,6 +698,7 @@ namespace gf2 {
 int identity_fill(int64_t *P, int64_t m, int64_t *Q, int64_t n, int64_t *rank, cudaStream_t s)
 {
     k_identity<<<64, 256, 0, s>>>(P, m, Q, n, rank);
+    prof_launched(1);
     return note_cuda(cudaGetLastError());
 }
 
@@ -702,12 +706,16 @@ int elim_run(const Elim &e)
 {
     const int m = (int)e.m;
     k_init<<<(m + 255) / 256, 256, 0, e.s>>>(e.A, e.stride, e.perm, e.side, e.st, m);
+    prof_launched(1);
     int rc = note_cuda(cudaGetLastError());
     if (rc)
         return rc;
     for (int b = 0; b < (int)e.W; ++b) {
         const int nbits = (int)((e.n - 64ll * b) < 64 ? (e.n - 64ll * b) : 64);
+        const int tok = prof_begin(e.s);
         k_pivot<<<1, 32, 0, e.s>>>(e.side + (size_t)(b & 1) * e.m, e.perm, e.st, e.P, e.Q, m, b, nbits);
+        prof_end(e.s, GF2_PROF_PIVOT, tok);
+        prof_launched(1);
         rc = note_cuda(cudaGetLastError());
         if (rc)
             return rc;
@@ -722,6 +730,7 @@ int elim_gather(const Elim &e, int64_t *rank)
 {
     k_gather<<<2 * sm_count(), 256, 0, e.s>>>(e.A, e.stride, e.perm, e.st, e.P, e.Q, e.out, e.ostride,
                                               (int)e.m, (int)e.n, (int)e.W, rank);
+    prof_launched(1);
     return note_cuda(cudaGetLastError());
 }
 
@@ -732,6 +741,7 @@ int pls_finish(const Elim &e)
         return note_cuda(err);
     k_pmask<<<64, 256, 0, e.s>>>(e.Q, e.st, e.pmask);
     k_compress<<<(int)((e.m + 127) / 128), 128, 0, e.s>>>(e.out, e.ostride, e.Q, e.pmask, e.st, (int)e.m);
+    prof_launched(2);
     int rc = note_cuda(cudaGetLastError());
     if (rc)
         return rc;

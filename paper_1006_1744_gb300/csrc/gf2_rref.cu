@@ -279,6 +279,7 @@ int rref_finish(const Elim &e, const ElimLayout &L, char *work, int64_t *rank, i
     k_rref_compact<<<(rmax + 127) / 128, 128, 0, e.s>>>(e.out, e.ostride, e.Q, e.pmask, e.st, e.A, Bc, sb, n, W);
     const int nblk = (rmax + 63) / 64;
     k_diag_inv<<<(nblk + 3) / 4, 128, 0, e.s>>>(e.A, e.stride, e.st, Dinv, nblk);
+    prof_launched(3);
     int rc = note_cuda(cudaGetLastError());
     if (rc)
         return rc;
@@ -292,13 +293,17 @@ int rref_finish(const Elim &e, const ElimLayout &L, char *work, int64_t *rank, i
         attr_set = true;
     }
     for (int q = nblk - 1; q >= 0; --q) {
+        const int tok = prof_begin(e.s);
         k_rref_step<<<grid, 256, smem, e.s>>>(Bc, Xc, sb, e.A, e.stride, Dinv, e.st, n, q);
+        prof_end(e.s, GF2_PROF_RREF, tok);
+        prof_launched(1);
         rc = note_cuda(cudaGetLastError());
         if (rc)
             return rc;
     }
     k_rref_scatter<<<(m + 127) / 128, 128, 0, e.s>>>(e.A, e.stride, Xc, sb, e.Q, e.pmask, e.st, m, n, W);
     k_rref_outputs<<<32, 256, 0, e.s>>>(e.Q, e.st, n, pivots, rank);
+    prof_launched(2);
     return note_cuda(cudaGetLastError());
 }
 

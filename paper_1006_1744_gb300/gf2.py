@@ -52,7 +52,33 @@ SYMBOLS = {
     "gf2_strerror": (ctypes.c_char_p, [_int]),
     "gf2_last_cuda_error": (_int, []),
     "gf2_version": (_int, []),
+    "gf2_prof_enable": (None, [_int]),
+    "gf2_prof_reset": (None, []),
+    "gf2_prof_launches": (ctypes.c_longlong, []),
+    "gf2_prof_collect": (_int, [_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
 }
+
+PROF_SWEEP, PROF_PIVOT, PROF_RREF, PROF_MUL = 0, 1, 2, 3
+
+
+def prof_enable(flags: int) -> None:
+    lib().gf2_prof_enable(flags)
+
+
+def prof_reset() -> None:
+    lib().gf2_prof_reset()
+
+
+def prof_launches() -> int:
+    return int(lib().gf2_prof_launches())
+
+
+def prof_collect(cls: int):
+    """(total milliseconds, launches) of one kernel class since prof_reset()."""
+    ms = ctypes.c_double(0)
+    n = ctypes.c_longlong(0)
+    _check(lib().gf2_prof_collect(cls, ctypes.byref(ms), ctypes.byref(n)), "gf2_prof_collect")
+    return ms.value, int(n.value)
 
 
 def lib_path() -> str:
