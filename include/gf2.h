@@ -58,6 +58,7 @@ extern "C" {
 #define GF2_ECUDA 4    /* a CUDA runtime call failed (see gf2_last_cuda_error) */
 #define GF2_ENOSPACE 5 /* work_bytes smaller than gf2_workspace_bytes() */
 #define GF2_EDIM 6     /* mismatched dimensions (gf2_mul) */
+#define GF2_ETOOBIG 7  /* matrix too large for the fixed scratch of gf2_rank_noalloc */
 
 /* op codes for gf2_workspace_bytes */
 #define GF2_OP_PLS 1
@@ -139,6 +140,30 @@ int gf2_rank(const uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *r
 int gf2_mul(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64_t *B, int64_t sb,
             int64_t m, int64_t k, int64_t n, int accumulate, void *work, size_t work_bytes,
             const gf2_opts *opts, void *stream);
+
+/*
+ * Rank without allocating device memory. The paper has no counterpart: this
+ * entry point exists for callers that may not call cudaMalloc -- code that runs
+ * while a CUDA graph is being captured, loops that cannot afford the device
+ * stall an allocation brings, and plug-ins whose host application owns all
+ * device memory. It computes exactly what gf2_rank computes (same arguments,
+ * A unchanged), but its workspace is one fixed array of
+ * GF2_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
+ * loads the library holds until the process exits. Nothing is allocated or
+ * freed by any call.
+ *   Limit: matrices whose rank workspace, gf2_workspace_bytes(GF2_OP_RANK, m,
+ *   n, NULL), exceeds GF2_NOALLOC_SCRATCH_BYTES (4 MiB; e.g. 4096 x 4096 fits)
+ *   are refused with GF2_ETOOBIG before anything is enqueued.
+ *   First call per device: looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Sharing: every call on a device uses that device's one array, which
+ *   keeps the last call's contents (each call re-initialises everything it
+ *   reads). Calls whose work can overlap on the GPU, e.g. on two streams of
+ *   the same device, race on the array; order them on one stream.
+ */
+#define GF2_NOALLOC_SCRATCH_BYTES (4u << 20)
+int gf2_rank_noalloc(const uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *rank, void *stream);
 
 /* Human-readable text for a GF2_* code (static storage). */
 const char *gf2_strerror(int code);

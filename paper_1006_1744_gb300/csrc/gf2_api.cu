@@ -323,6 +323,8 @@ const char *gf2_strerror(int code)
         return "workspace smaller than gf2_workspace_bytes()";
     case GF2_EDIM:
         return "mismatched dimensions";
+    case GF2_ETOOBIG:
+        return "matrix too large for the fixed scratch of gf2_rank_noalloc (GF2_NOALLOC_SCRATCH_BYTES)";
     default:
         return "unknown error";
     }

@@ -52,6 +52,7 @@ SYMBOLS = {
     "gf2_strerror": (ctypes.c_char_p, [_int]),
     "gf2_last_cuda_error": (_int, []),
     "gf2_version": (_int, []),
+    "gf2_rank_noalloc": (_int, [_vp, _i64, _i64, _i64, _vp, _vp]),
     "gf2_prof_enable": (None, [_int]),
     "gf2_prof_reset": (None, []),
     "gf2_prof_launches": (ctypes.c_longlong, []),
@@ -191,6 +192,14 @@ def rank(A: torch.Tensor, n: int, rank=None, work=None, opts=None, stream=None):
     wp, wb = _work(work)
     _check(lib().gf2_rank(_ptr(A), m, n, stride, _ptr(rank), wp, wb, _opts(opts), _stream(stream)),
            "gf2_rank")
+    return rank
+
+
+def rank_noalloc(A: torch.Tensor, n: int, rank=None, stream=None):
+    """Rank using the library's fixed scratch array instead of any allocation."""
+    m, stride = _mat(A, n, "gf2_rank_noalloc")
+    rank = torch.empty(1, dtype=torch.int64, device=A.device) if rank is None else rank
+    _check(lib().gf2_rank_noalloc(_ptr(A), m, n, stride, _ptr(rank), _stream(stream)), "gf2_rank_noalloc")
     return rank
 
 
