@@ -27,10 +27,10 @@ struct PanelState {
     u64 J;          // pivot columns of the panel, as a bit mask of the panel word
     int prow[64];   // physical row of pivot t (rows are never moved during elimination)
     int pcol[64];   // panel-relative column of pivot t
-    u64 zmap[64];   // column c of the panel -> O-coordinates of the reduced basis row with a 1 at c
-    u64 xmap[64];   // column c -> multipliers of L (scattered to pivot columns) of that basis row
-    u64 zpiv[64];   // pivot t -> O-coordinates of its fully reduced row U_t
     u64 newblk[64]; // pivot t -> its final panel word (U_t plus its own multipliers)
+    u64 zpiv[64];   // pivot t -> row t of L^-1: U_t as a sum of the ORIGINAL pivot rows O
+    u64 zmap[64];   // column c -> row of (O_J)^-1 = U_J^-1 L^-1 for the pivot at c (0 elsewhere)
+    u64 xmap[64];   // column c -> row of U_J^-1 for the pivot at c, scattered to the pivot columns
 };
 
 // ---------------------------------------------------------------------------

@@ -46,283 +46,568 @@ __global__ void k_init(const uint64_t *__restrict__ A, int64_t stride, int *__re
 // ---------------------------------------------------------------------------
 // Pivot search of panel b (one warp).
 //
-// Rows at positions >= r are candidates. Each holds its panel word w (as left
-// by the previous panels), reduced by the pivots found so far in this panel.
-// Pivot t is the smallest column j > j_{t-1} with a 1 in some candidate, and
-// among those the candidate with the smallest position: exactly the rule of
-// the Gaussian PLS algorithm restricted to this panel. The first WIN positions
-// live in registers and are reduced incrementally; positions beyond are only
-// scanned (reduced from scratch) when no windowed row has a 1 in the next
-// column, which is rare for dense inputs.
+// Rows at positions >= r are candidates. Pivot t is the smallest column
+// j > j_{t-1} with a 1 in some candidate (reduced by the pivots found so far in
+// this panel), and among those the candidate with the smallest position:
+// exactly the rule of the Gaussian PLS algorithm restricted to this panel.
 //
-// Bookkeeping per row: x = its multipliers (bit s: pivot s was added, i.e. the
-// entry of L), z = its coordinates over the ORIGINAL panel words O of the
-// pivot rows (reduced word = w + z.O). The pivots are also kept in
-// Gauss-Jordan form V (1 at their own column, 0 at the other pivot columns),
-// which gives, for any later row, its multipliers and coordinates straight
-// from the bits of its raw panel word (zmap, xmap) -- the table sweep needs
-// nothing else.
+// Outputs per pivot t: its physical row, position (P) and column (Q), its
+// final panel word (the Gaussian PLS row: multipliers of L left of its pivot,
+// the reduced bits right of it) and its multipliers as a bit vector over the
+// earlier pivots; per pivot column: the row of U_J^-1 (U_J = the pivots'
+// reduced rows at the pivot columns), which turns the raw panel word of any
+// later row into its multipliers.
+//
+// Fast path (pivot_fast): the first WIN = 128 positions in column form. Lane l
+// holds columns l and l+32 as 128-bit vectors over the positions, so a pivot
+// costs one shuffle of the pivot column, a swap of two bits and a masked XOR
+// per column; the Gauss-Jordan bits of the pivot rows give the columns of
+// U_J^-1 as a by-product. If a column has no candidate in the window while
+// rows exist past it, the panel is redone by the row-form path (pivot_rows),
+// which also scans past the window.
 // ---------------------------------------------------------------------------
+constexpr int GROUP = 8;  // columns per group step of the row-form path
+constexpr int SW = 16;    // rows of the prefix eliminated per group step
+
+// 32 x 32 bit transpose across a warp: lane i holds row i on input, lane c
+// holds column c on output (five butterfly exchanges).
+__device__ __forceinline__ unsigned bt32(unsigned x, int lane)
+{
+    const unsigned masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int j = 16 >> k;
+        const unsigned m = masks[k];
+        const unsigned y = __shfl_xor_sync(GF2_FULL, x, j);
+        x = (lane & j) ? ((x & ~m) | ((y >> j) & m)) : ((x & m) | ((y & m) << j));
+    }
+    return x;
+}
+
+// exchange bits t (< 64) and p (< 128) of the 128-bit value (lo, hi)
+__device__ __forceinline__ void swap_rows128(u64 &lo, u64 &hi, int t, int p)
+{
+    if (p < 64) {
+        const u64 d = ((lo >> t) ^ (lo >> p)) & 1ull;
+        lo ^= (d << t) | (d << p);
+    } else {
+        const u64 d = ((lo >> t) ^ (hi >> (p - 64))) & 1ull;
+        lo ^= d << t;
+        hi ^= d << (p - 64);
+    }
+}
+
+struct PivotShared {
+    // window, indexed by position - r (row form)
+    u64 Ww[WIN], Wx[WIN];
+    int Wph[WIN];
+    // Gauss-Jordan basis of the pivots so far (row form): word, U-coordinates, column
+    u64 sVw[64], sVx[64];
+    int sVc[64], sC2P[64];
+    // results: final panel word, multipliers, rows of U_J^-1 and L^-1, position, column of each pivot
+    u64 sNew[64], sXl[64], sUi[64], sLi[64];
+    int sPpos[64], sPcol[64];
+    // group scratch of the row-form path
+    u64 TVw[256], TVx[256];
+    u64 gVw[GROUP], gVx[GROUP];
+    int gIpos[GROUP], gX8[GROUP], gLinv[GROUP], gMm[GROUP], gUinv[GROUP];
+};
+
+__device__ bool pivot_fast(const u64 *__restrict__ side, const int *__restrict__ perm, int r, int m, int nwin,
+                           int nbits, int &t_out, u64 &J_out, PivotShared &S)
+{
+    const int lane = threadIdx.x;
+    u64 rows[NSLOT];
+#pragma unroll
+    for (int k = 0; k < NSLOT; ++k) {
+        const int i = lane + 32 * k;
+        int ph = 0;
+        u64 w = 0;
+        if (i < nwin) {
+            ph = perm[r + i];
+            w = side[ph];
+        }
+        S.Wph[i] = ph;
+        rows[k] = w;
+    }
+    // column form: lane l <- columns l (c0) and l + 32 (c1) over positions 0..127
+    unsigned tc[NSLOT][2];
+#pragma unroll
+    for (int k = 0; k < NSLOT; ++k) {
+        tc[k][0] = bt32((unsigned)rows[k], lane);
+        tc[k][1] = bt32((unsigned)(rows[k] >> 32), lane);
+    }
+    u64 c0l = (u64)tc[0][0] | ((u64)tc[1][0] << 32), c0h = (u64)tc[2][0] | ((u64)tc[3][0] << 32);
+    u64 c1l = (u64)tc[0][1] | ((u64)tc[1][1] << 32), c1h = (u64)tc[2][1] | ((u64)tc[3][1] << 32);
+    u64 G0 = 0, G1 = 0;  // Gauss-Jordan pivot rows at columns lane, lane + 32 (bit s = pivot s)
+    u64 X0 = 0, X1 = 0;  // columns lane, lane + 32 of U_J^-1 (bit s = row s)
+    u64 L0 = 0, L1 = 0;  // columns lane, lane + 32 of L^-1 (bit s = row s)
+    const bool all_rows = (m - r) <= WIN;
+    int t = 0, j = 0;
+    u64 J = 0, tb = 1;
+    while (t < 64 && j < nbits && t < nwin) {
+        const int jl = j & 31;
+        const bool jh = j >= 32;
+        const u64 cl = jh ? c1l : c0l, ch = jh ? c1h : c0h;
+        const u64 cand = cl & ~(tb - 1ull);
+        const int pm = cand ? ctz64(cand) : (ch ? 64 + ctz64(ch) : 255);
+        const int p = __shfl_sync(GF2_FULL, pm, jl);
+        u64 cjl = __shfl_sync(GF2_FULL, cl, jl);
+        u64 cjh = __shfl_sync(GF2_FULL, ch, jl);
+        const u64 gj = __shfl_sync(GF2_FULL, jh ? G1 : G0, jl);
+        if (p >= nwin) {
+            if (!all_rows)
+                return false;  // a candidate may sit past the window
+            ++j;               // zero column among all remaining rows
+            continue;
+        }
+        if (p != t) {
+            swap_rows128(c0l, c0h, t, p);
+            swap_rows128(c1l, c1h, t, p);
+            swap_rows128(cjl, cjh, t, p);
+            if (lane == 0) {
+                const int q = S.Wph[t];
+                S.Wph[t] = S.Wph[p];
+                S.Wph[p] = q;
+            }
+        }
+        if (lane == 0) {
+            S.sPpos[t] = r + p;
+            S.sPcol[t] = j;
+        }
+        // rows below the pivot with a 1 in column j get the pivot row on columns > j
+        const u64 rl = cjl & ~((tb << 1) - 1ull), rh = cjh;
+        const bool pb0 = (c0l & tb) != 0, pb1 = (c1l & tb) != 0;  // pivot row's bits at my columns
+        const u64 k0 = (lane > j && pb0) ? ~0ull : 0ull;
+        const u64 k1 = (lane + 32 > j && pb1) ? ~0ull : 0ull;
+        c0l ^= rl & k0;
+        c0h ^= rh & k0;
+        c1l ^= rl & k1;
+        c1h ^= rh & k1;
+        // Gauss-Jordan: pivot row t joins, column j is cleared from the earlier ones;
+        // column t of U_J^-1 is the set of earlier rows that were cleared, plus t
+        G0 |= pb0 ? tb : 0ull;
+        G1 |= pb1 ? tb : 0ull;
+        const u64 mu = gj & (tb - 1ull);
+        G0 ^= (G0 & tb) ? mu : 0ull;
+        G1 ^= (G1 & tb) ? mu : 0ull;
+        if (lane == (t & 31)) {
+            if (t < 32)
+                X0 = mu | tb;
+            else
+                X1 = mu | tb;
+        }
+        // multipliers of pivot row t (its bits at the earlier pivot columns) and row t of
+        // L^-1: L^-1[t] = e_t + sum of the L^-1[s] its multipliers select
+        const u64 rowbits = (u64)__ballot_sync(GF2_FULL, pb0) | ((u64)__ballot_sync(GF2_FULL, pb1) << 32);
+        const u64 left = rowbits & ((1ull << j) - 1ull);
+        const u64 xlt = (J == tb - 1ull) ? left : pext64(left, J);
+        if (lane == 0)
+            S.sXl[t] = xlt;
+        L0 |= (((u64)(__popcll(xlt & L0) & 1)) << t) | ((u64)(lane == t) << t);
+        L1 |= (((u64)(__popcll(xlt & L1) & 1)) << t) | ((u64)(lane + 32 == t) << t);
+        J |= 1ull << j;
+        ++j;
+        ++t;
+        tb <<= 1;
+    }
+    // back to row form: pivot rows (positions < 64) and rows of U_J^-1
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const u64 rw = (u64)bt32((unsigned)(c0l >> (32 * k)), lane) |
+                       ((u64)bt32((unsigned)(c1l >> (32 * k)), lane) << 32);
+        const u64 ui = (u64)bt32((unsigned)(X0 >> (32 * k)), lane) |
+                       ((u64)bt32((unsigned)(X1 >> (32 * k)), lane) << 32);
+        const u64 li = (u64)bt32((unsigned)(L0 >> (32 * k)), lane) |
+                       ((u64)bt32((unsigned)(L1 >> (32 * k)), lane) << 32);
+        const int s2 = lane + 32 * k;
+        if (s2 < t) {
+            S.sNew[s2] = rw;
+            S.sUi[s2] = ui;
+            S.sLi[s2] = li;
+        }
+    }
+    t_out = t;
+    J_out = J;
+    return true;
+}
+
+// Row-form path: window rows in shared memory indexed by position, pivots taken
+// GROUP columns at a time when the first SW candidate rows hold a 1 in each of
+// them (a contiguous prefix of the row order, so a 1 found there is the first
+// one in its column), one at a time otherwise, with rows past the window
+// reduced from scratch by the Gauss-Jordan basis.
+__device__ void pivot_rows(const u64 *__restrict__ side, int *__restrict__ perm, int r, int m, int nwin, int nbits,
+                           int &t_out, u64 &J_out, PivotShared &S)
+{
+    const int lane = threadIdx.x;
+    int t = 0;
+    u64 J = 0;
+    for (int i = lane; i < nwin; i += 32) {
+        const int ph = perm[r + i];
+        S.Wph[i] = ph;
+        S.Ww[i] = side[ph];
+        S.Wx[i] = 0;
+    }
+    __syncwarp();
+    int jlow = 0;
+    while (nwin > 0 && t < 64 && jlow < nbits && r + t < m) {
+        const int kbmax = min(GROUP, nbits - jlow);
+        // ---------------- group step: the first SW candidate rows, GROUP columns ----------------
+        {
+            const bool rv = lane < SW && t + lane < nwin;
+            int sl = rv ? (int)((S.Ww[t + lane] >> jlow) & (u64)((1u << kbmax) - 1u)) : 0;
+            int pos = lane;   // position in the prefix (current order)
+            int comb = 0;     // raw pivot rows in this row's reduced slice
+            int mul = 0;      // multipliers for the group's pivots
+            int pidx = -1;    // pivot index within the group, once chosen
+            int gjb = 0, gjc = 0, gju = 0;  // Gauss-Jordan row: slice, raw-row combination, U-coordinates
+            int lcomb = 0, lmul = 0, lpos = 0;
+            int kb = 0;
+            for (int c = 0; c < kbmax; ++c) {
+                const bool cand = rv && pidx < 0 && ((sl >> c) & 1);
+                const int kmin = __reduce_min_sync(GF2_FULL, cand ? pos : 1 << 20);
+                if (kmin >= (1 << 20))
+                    break;
+                const int owner = __ffs(__ballot_sync(GF2_FULL, cand && pos == kmin)) - 1;
+                const int pv = __shfl_sync(GF2_FULL, sl, owner);
+                const int lc = __shfl_sync(GF2_FULL, comb, owner) | (1 << c);
+                if (lane == owner) {
+                    lpos = kmin;
+                    lcomb = lc;
+                    lmul = mul;
+                    pidx = c;
+                    gjb = pv;
+                    gjc = lc;
+                    gju = 1 << c;
+                } else if (pidx < 0 && pos == c) {
+                    pos = kmin;  // the head row takes the pivot's old position
+                }
+                if (lane == owner)
+                    pos = c;
+                if (pidx < 0 && rv && pos > c && ((sl >> c) & 1)) {
+                    sl ^= pv;
+                    comb ^= lc;
+                    mul |= 1 << c;
+                }
+                if (pidx >= 0 && pidx < c && ((gjb >> c) & 1)) {
+                    gjb ^= pv;
+                    gjc ^= lc;
+                    gju ^= 1 << c;
+                }
+                kb = c + 1;
+            }
+            if (kb > 0) {
+                u64 mw = 0, mx = 0;
+                int mph = 0;
+                if (rv) {
+                    mw = S.Ww[t + lane];
+                    mx = S.Wx[t + lane];
+                    mph = S.Wph[t + lane];
+                }
+                __syncwarp();
+                if (rv) {
+                    S.Ww[t + pos] = mw;
+                    S.Wx[t + pos] = mx;
+                    S.Wph[t + pos] = mph;
+                }
+                if (pidx >= 0) {
+                    S.gIpos[pidx] = lpos;
+                    S.gX8[pidx] = lmul;
+                    S.gLinv[pidx] = lcomb;
+                    S.gMm[pidx] = gjc;
+                    S.gUinv[pidx] = gju;
+                }
+                __syncwarp();
+                u64 rw8[GROUP];
+#pragma unroll
+                for (int c2 = 0; c2 < GROUP; ++c2)
+                    rw8[c2] = c2 < kb ? S.Ww[t + c2] : 0ull;
+                if (lane < kb) {
+                    const int c = lane;
+                    const int li = S.gLinv[c], mi = S.gMm[c];
+                    u64 uw = 0, vw = 0;
+#pragma unroll
+                    for (int c2 = 0; c2 < GROUP; ++c2) {
+                        if ((li >> c2) & 1)
+                            uw ^= rw8[c2];
+                        if ((mi >> c2) & 1)
+                            vw ^= rw8[c2];
+                    }
+                    const u64 xl = S.Wx[t + c] | ((u64)S.gX8[c] << t);
+                    // scatter the multipliers over the pivot columns so far, this group's included
+                    S.sNew[t + c] = uw | pdep64(xl, J | ((((u64)1 << kb) - 1ull) << jlow));
+                    S.sXl[t + c] = xl;
+                    S.sPpos[t + c] = r + t + S.gIpos[c];
+                    S.sPcol[t + c] = jlow + c;
+                    S.gVw[c] = vw;
+                    S.gVx[c] = (u64)S.gUinv[c] << t;
+                }
+                __syncwarp();
+                u64 vw8[GROUP], vx8[GROUP];
+#pragma unroll
+                for (int c = 0; c < GROUP; ++c) {
+                    vw8[c] = c < kb ? S.gVw[c] : 0ull;
+                    vx8[c] = c < kb ? S.gVx[c] : 0ull;
+                }
+                const int nt = 1 << kb;
+                if (8 * lane < nt || lane == 0) {
+                    u64 aw = 0, ax = 0;
+#pragma unroll
+                    for (int c = 3; c < GROUP; ++c)
+                        if ((lane >> (c - 3)) & 1) {
+                            aw ^= vw8[c];
+                            ax ^= vx8[c];
+                        }
+                    const int base = 8 * lane;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        if (i) {
+                            const int f = (i & 1) ? 0 : ((i & 2) ? 1 : 2);  // lowest set bit of i
+                            aw ^= vw8[f];
+                            ax ^= vx8[f];
+                        }
+                        const int v = base + (i ^ (i >> 1));
+                        if (v < nt) {
+                            S.TVw[v] = aw;
+                            S.TVx[v] = ax;
+                        }
+                    }
+                }
+                __syncwarp();
+                const u64 msk = (u64)(nt - 1);
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int s2 = lane + 32 * k;
+                    if (s2 < t) {
+                        const int bb = (int)((S.sVw[s2] >> jlow) & msk);
+                        S.sVw[s2] ^= S.TVw[bb];
+                        S.sVx[s2] ^= S.TVx[bb];
+                    }
+                }
+                if (lane < kb) {
+                    S.sVw[t + lane] = S.gVw[lane];
+                    S.sVx[t + lane] = S.gVx[lane];
+                    S.sVc[t + lane] = jlow + lane;
+                    S.sC2P[jlow + lane] = t + lane;
+                }
+                u64 ww[NSLOT];
+                int bbk[NSLOT];
+#pragma unroll
+                for (int k = 0; k < NSLOT; ++k) {
+                    const int i = t + kb + lane + 32 * k;
+                    ww[k] = i < nwin ? S.Ww[i] : 0ull;
+                    bbk[k] = (int)((ww[k] >> jlow) & msk);
+                }
+#pragma unroll
+                for (int k = 0; k < NSLOT; ++k) {
+                    const int i = t + kb + lane + 32 * k;
+                    if (i < nwin) {
+                        S.Ww[i] = ww[k] ^ S.TVw[bbk[k]];
+                        S.Wx[i] ^= S.TVx[bbk[k]];
+                    }
+                }
+                __syncwarp();
+                t += kb;
+                J |= msk << jlow;
+                jlow += kb;
+            }
+            if (kb == kbmax)
+                continue;
+            if (!(t < 64 && jlow < nbits && r + t < m))
+                break;
+        }
+        // ---------------- general step: one pivot, any column >= jlow ----------------
+        int key = INT_MAX;
+        for (int i = t + lane; i < nwin; i += 32)
+            if ((S.Ww[i] >> jlow) & 1ull) {
+                key = i;
+                break;
+            }
+        const int best = __reduce_min_sync(GF2_FULL, key);
+        int pc, pos;
+        bool from_out = false;
+        u64 ow = 0, ox = 0;
+        int oph = -1;
+        if (best != INT_MAX) {
+            pc = jlow;
+            pos = r + best;
+        } else {
+            int myc = 64, myi = INT_MAX;
+            for (int i = t + lane; i < nwin; i += 32) {
+                const u64 mk = S.Ww[i] & ~lowmask(jlow);
+                const int c = mk ? ctz64(mk) : 64;
+                if (c < myc) {
+                    myc = c;
+                    myi = i;
+                }
+            }
+            const int cw = __reduce_min_sync(GF2_FULL, myc);
+            const int iw = __reduce_min_sync(GF2_FULL, myc == cw ? myi : INT_MAX);
+            int bc = cw, bl = cw < 64 ? r + iw : INT_MAX;
+            for (int p0 = r + WIN; p0 < m && !(bc == jlow && p0 >= bl); p0 += 32) {
+                const int p = p0 + lane;
+                int c = 64, phh = -1;
+                u64 ww = 0, xx = 0;
+                if (p < m) {
+                    phh = perm[p];
+                    ww = side[phh];
+                    u64 pm = ww & J;
+                    while (pm) {
+                        const int cc = ctz64(pm);
+                        pm &= pm - 1;
+                        const int sidx = S.sC2P[cc];
+                        ww ^= S.sVw[sidx];
+                        xx ^= S.sVx[sidx];
+                    }
+                    const u64 mk = ww & ~lowmask(jlow);
+                    c = mk ? ctz64(mk) : 64;
+                }
+                const int cc = __reduce_min_sync(GF2_FULL, c);
+                if (cc < 64) {
+                    const int cp = __reduce_min_sync(GF2_FULL, c == cc ? p : INT_MAX);
+                    if (cc < bc || (cc == bc && cp < bl)) {
+                        const int src = cp - p0;
+                        bc = cc;
+                        bl = cp;
+                        from_out = true;
+                        ow = __shfl_sync(GF2_FULL, ww, src);
+                        ox = __shfl_sync(GF2_FULL, xx, src);
+                        oph = __shfl_sync(GF2_FULL, phh, src);
+                    }
+                }
+            }
+            if (bc == 64)
+                break;  // no further pivot in this panel
+            pc = bc;
+            pos = bl;
+        }
+        if (lane == 0) {
+            if (from_out) {
+                perm[pos] = S.Wph[t];  // the head row takes the pivot's old position
+                S.Ww[t] = ow;
+                S.Wx[t] = ox;
+                S.Wph[t] = oph;
+            } else if (pos != r + t) {
+                const int i = pos - r;
+                u64 a = S.Ww[t];
+                S.Ww[t] = S.Ww[i];
+                S.Ww[i] = a;
+                a = S.Wx[t];
+                S.Wx[t] = S.Wx[i];
+                S.Wx[i] = a;
+                const int q = S.Wph[t];
+                S.Wph[t] = S.Wph[i];
+                S.Wph[i] = q;
+            }
+        }
+        __syncwarp();
+        const u64 pw = S.Ww[t], tb = 1ull << t;
+        if (lane == 0) {
+            S.sNew[t] = pw | pdep64(S.Wx[t], J);
+            S.sXl[t] = S.Wx[t];
+            S.sPpos[t] = pos;
+            S.sPcol[t] = pc;
+        }
+        for (int s2 = lane; s2 < t; s2 += 32)
+            if ((S.sVw[s2] >> pc) & 1ull) {
+                S.sVw[s2] ^= pw;
+                S.sVx[s2] ^= tb;
+            }
+        if (lane == 0) {
+            S.sVw[t] = pw;
+            S.sVx[t] = tb;
+            S.sVc[t] = pc;
+            S.sC2P[pc] = t;
+        }
+        for (int i = t + 1 + lane; i < nwin; i += 32)
+            if ((S.Ww[i] >> pc) & 1ull) {
+                S.Ww[i] ^= pw;
+                S.Wx[i] |= tb;
+            }
+        __syncwarp();
+        J |= 1ull << pc;
+        jlow = pc + 1;
+        ++t;
+    }
+    __syncwarp();
+    // rows of U_J^-1 are the U-coordinates of the Gauss-Jordan rows
+    for (int s2 = lane; s2 < t; s2 += 32)
+        S.sUi[s2] = S.sVx[s2];
+    t_out = t;
+    J_out = J;
+}
+
 __global__ void __launch_bounds__(32, 1)
 k_pivot(const u64 *__restrict__ side, int *__restrict__ perm, PanelState *st, int64_t *P,
         int64_t *Q, int m, int b, int nbits)
 {
-    // pivot records, written by the lane that held the pivot row
-    __shared__ u64 sUw[64], sXp[64], sZp[64];
-    __shared__ int sProw[64];
-    // basis and column map, materialised only for scans past the window and at the end
-    __shared__ u64 sVw[64], sVz[64], sVx[64];
-    __shared__ int sC2P[64];
-    __shared__ u64 sZm[64], sXm[64];
-
+    __shared__ PivotShared S;
+    __shared__ u64 sXp[64], sXm[64];
     const int lane = threadIdx.x;
     const int r = st->r_next;
     int t = 0;
     u64 J = 0;
-    // basis rows s = lane (j = 0) and s = lane + 32 (j = 1), Gauss-Jordan form
-    u64 vw[2] = {0, 0}, vz[2] = {0, 0}, vx[2] = {0, 0};
-    int vc[2] = {0, 0};
-    int pp[2] = {0, 0};  // P entries of pivots lane and lane + 32: position the row came from
-
-    if (r < m && !st->zero_tail) {
-        u64 w[NSLOT], z[NSLOT], x[NSLOT];
-        int lab[NSLOT], ph[NSLOT], pt[NSLOT];  // pt: pivot index a slot became (-1: none)
-        bool act[NSLOT];
-#pragma unroll
-        for (int k = 0; k < NSLOT; ++k) {
-            int p = r + lane + 32 * k;
-            pt[k] = -1;
-            act[k] = p < m;
-            lab[k] = p;
-            ph[k] = act[k] ? perm[p] : -1;
-            w[k] = act[k] ? side[ph[k]] : 0ull;
-            z[k] = 0ull;
-            x[k] = 0ull;
-        }
-        int jlow = 0;
-        while (t < 64 && jlow < nbits && r + t < m) {
-            // (1) windowed candidate with a 1 at column jlow and the smallest position;
-            // key = (position - r) * 32 + lane, positions past the window collapse to WIN
-            int key = INT_MAX, myk = 0;
-            u64 tw = 0, tz = 0;
-#pragma unroll
-            for (int k = 0; k < NSLOT; ++k)
-                if (act[k] && ((w[k] >> jlow) & 1ull)) {
-                    const int rel = lab[k] - r;
-                    const int kk = rel < WIN ? ((rel << 5) | lane) : (WIN << 5);
-                    if (kk < key) {
-                        key = kk;
-                        myk = k;
-                        tw = w[k];
-                        tz = z[k];
-                    }
-                }
-            const int best = __reduce_min_sync(GF2_FULL, key);
-            int pc, plab, owner = -1;
-            bool from_out = false;
-            u64 pw = 0, ut = 0;
-            if (best < (WIN << 5)) {
-                // every position past the window is larger than one inside it
-                pc = jlow;
-                plab = r + (best >> 5);
-                owner = best & 31;
-            } else {
-                // (2) slow path: materialise the basis for from-scratch reductions
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int sidx = lane + 32 * j;
-                    if (sidx < t) {
-                        sVw[sidx] = vw[j];
-                        sVz[sidx] = vz[j];
-                        sVx[sidx] = vx[j];
-                        sC2P[vc[j]] = sidx;
-                    }
-                }
-                __syncwarp();
-                // (2a) smallest (column, position) among windowed rows (a windowed row
-                // may carry a label past the window after an earlier swap)
-                int myc = 64, mylab = INT_MAX, myk2 = 0;
-#pragma unroll
-                for (int k = 0; k < NSLOT; ++k) {
-                    if (!act[k])
-                        continue;
-                    u64 mk = w[k] & ~lowmask(jlow);
-                    int c = mk ? ctz64(mk) : 64;
-                    if (c < myc || (c == myc && lab[k] < mylab)) {
-                        myc = c;
-                        mylab = lab[k];
-                        myk2 = k;
-                    }
-                }
-                const int cw = __reduce_min_sync(GF2_FULL, myc);
-                int lw = __reduce_min_sync(GF2_FULL, myc == cw ? mylab : INT_MAX);
-                if (cw == 64)
-                    lw = INT_MAX;
-                // (2b) rows past the window, reduced from scratch by the basis
-                int bc = cw, bl = lw;
-                u64 ow = 0, oz = 0, ox = 0;
-                int oph = -1;
-                for (int p0 = r + WIN; p0 < m && !(bc == jlow && p0 >= bl); p0 += 32) {
-                    const int p = p0 + lane;
-                    int c = 64, phh = -1;
-                    u64 ww = 0, zz = 0, xx = 0;
-                    if (p < m) {
-                        phh = perm[p];
-                        ww = side[phh];
-                        u64 pm = ww & J;
-                        while (pm) {
-                            int cc = ctz64(pm);
-                            pm &= pm - 1;
-                            int sidx = sC2P[cc];
-                            ww ^= sVw[sidx];
-                            zz ^= sVz[sidx];
-                            xx ^= sVx[sidx];
-                        }
-                        u64 mk = ww & ~lowmask(jlow);
-                        c = mk ? ctz64(mk) : 64;
-                    }
-                    const int cc = __reduce_min_sync(GF2_FULL, c);
-                    if (cc < 64) {
-                        const int cp = __reduce_min_sync(GF2_FULL, c == cc ? p : INT_MAX);
-                        if (cc < bc || (cc == bc && cp < bl)) {
-                            const int src = cp - p0;
-                            bc = cc;
-                            bl = cp;
-                            from_out = true;
-                            ow = __shfl_sync(GF2_FULL, ww, src);
-                            oz = __shfl_sync(GF2_FULL, zz, src);
-                            ox = __shfl_sync(GF2_FULL, xx, src);
-                            oph = __shfl_sync(GF2_FULL, phh, src);
-                        }
-                    }
-                }
-                if (bc == 64)
-                    break;  // no further pivot in this panel
-                pc = bc;
-                plab = bl;
-                if (from_out) {
-                    pw = ow;
-                    ut = oz ^ (1ull << t);
-                    if (lane == 0) {
-                        sUw[t] = ow;
-                        sXp[t] = ox;
-                        sZp[t] = oz;
-                        sProw[t] = oph;
-                    }
-                } else {
-                    owner = __ffs(__ballot_sync(GF2_FULL, myc == cw && mylab == bl)) - 1;
-                    myk = myk2;
-#pragma unroll
-                    for (int k = 0; k < NSLOT; ++k)
-                        if (k == myk2) {
-                            tw = w[k];
-                            tz = z[k];
-                        }
-                }
-            }
-            if (!from_out) {
-                // the owner's slot becomes pivot t; its registers stay frozen from now on and
-                // its records are written after the loop
-                pw = __shfl_sync(GF2_FULL, tw, owner);
-                ut = __shfl_sync(GF2_FULL, tz, owner) ^ (1ull << t);
-                const bool mine = lane == owner;
-#pragma unroll
-                for (int k = 0; k < NSLOT; ++k) {
-                    const bool sel = mine && k == myk;
-                    pt[k] = sel ? t : pt[k];
-                    act[k] = act[k] && !sel;
-                }
-            }
-            // (3) swap positions r+t and plab (logically)
-            const int h = r + t;
-            if (plab != h) {
-#pragma unroll
-                for (int k = 0; k < NSLOT; ++k)
-                    if (act[k] && lab[k] == h) {
-                        lab[k] = plab;
-                        if (plab >= r + WIN)  // keep perm exact for later scans past the window
-                            perm[plab] = ph[k];
-                    }
-            }
-            // (4) Gauss-Jordan: clear column pc from the earlier basis rows, add row t
-            const u64 tb = 1ull << t;
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int sidx = lane + 32 * j;
-                if (sidx < t && ((vw[j] >> pc) & 1ull)) {
-                    vw[j] ^= pw;
-                    vz[j] ^= ut;
-                    vx[j] ^= tb;
-                }
-                if (sidx == t) {
-                    vw[j] = pw;
-                    vz[j] = ut;
-                    vx[j] = tb;
-                    vc[j] = pc;
-                    pp[j] = plab;
-                }
-            }
-            // (5) reduce the windowed candidates
-#pragma unroll
-            for (int k = 0; k < NSLOT; ++k)
-                if (act[k] && ((w[k] >> pc) & 1ull)) {
-                    w[k] ^= pw;
-                    z[k] ^= ut;
-                    x[k] |= tb;
-                }
-            J |= 1ull << pc;
-            jlow = pc + 1;
-            ++t;
-        }
-        // records of the pivots taken from the window (pivots from past the window were
-        // recorded by lane 0 when they were found); the row of pivot t sits at position r+t
-#pragma unroll
-        for (int k = 0; k < NSLOT; ++k)
-            if (pt[k] >= 0) {
-                sUw[pt[k]] = w[k];
-                sXp[pt[k]] = x[k];
-                sZp[pt[k]] = z[k];
-                sProw[pt[k]] = ph[k];
-            }
+    const int nwin = (r < m && !st->zero_tail) ? min(WIN, m - r) : 0;
+    if (nwin > 0) {
+        const bool fast = pivot_fast(side, perm, r, m, nwin, nbits, t, J, S);
         __syncwarp();
-        // row order of the window back to memory
+        if (!fast) {
+            pivot_rows(side, perm, r, m, nwin, nbits, t, J, S);
+            __syncwarp();
+            // columns k = lane, lane + 32 of L^-1 from the multipliers, row by row
+            u64 L0 = 0, L1 = 0;
+            for (int s2 = 0; s2 < t; ++s2) {
+                const u64 xl = S.sXl[s2], tb = 1ull << s2;
+                L0 |= (((u64)(__popcll(xl & L0) & 1)) << s2) | (lane == s2 ? tb : 0ull);
+                L1 |= (((u64)(__popcll(xl & L1) & 1)) << s2) | (lane + 32 == s2 ? tb : 0ull);
+            }
 #pragma unroll
-        for (int k = 0; k < NSLOT; ++k)
-            if (act[k])
-                perm[lab[k]] = ph[k];
-        for (int s = lane; s < t; s += 32)
-            perm[r + s] = sProw[s];
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-            if (P && lane + 32 * j < t)
-                P[r + lane + 32 * j] = pp[j];
+            for (int k = 0; k < 2; ++k) {
+                const u64 li = (u64)bt32((unsigned)(L0 >> (32 * k)), lane) |
+                               ((u64)bt32((unsigned)(L1 >> (32 * k)), lane) << 32);
+                if (lane + 32 * k < t)
+                    S.sLi[lane + 32 * k] = li;
+            }
+        }
     }
-    // maps for the sweep: column c -> coordinates / multipliers of the basis row with its 1 at c
-    sZm[lane] = 0;
-    sZm[lane + 32] = 0;
+    __syncwarp();
+    // row order of the window, P and Q
+    for (int i = lane; i < nwin; i += 32)
+        perm[r + i] = S.Wph[i];
+    for (int s2 = lane; s2 < t; s2 += 32) {
+        if (P)
+            P[r + s2] = S.sPpos[s2];
+        if (Q)
+            Q[r + s2] = 64ll * b + S.sPcol[s2];
+    }
+    // maps for the sweep, by pivot column: row of M = U_J^-1 L^-1 (= (O_J)^-1: raw panel bits ->
+    // coordinates over the original pivot rows) and the row of U_J^-1 scattered to the pivot columns
+    sXp[lane] = 0;
+    sXp[lane + 32] = 0;
     sXm[lane] = 0;
     sXm[lane + 32] = 0;
     __syncwarp();
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const int sidx = lane + 32 * j;
-        if (sidx < t) {
-            sZm[vc[j]] = vz[j];
-            sXm[vc[j]] = pdep64(vx[j], J);
-            st->pcol[sidx] = vc[j];
-            if (Q)
-                Q[r + sidx] = 64ll * b + vc[j];
+    for (int s2 = lane; s2 < t; s2 += 32) {
+        u64 ui = S.sUi[s2], mrow = 0;
+        while (ui) {
+            const int k = ctz64(ui);
+            ui &= ui - 1;
+            mrow ^= S.sLi[k];
         }
+        sXp[S.sPcol[s2]] = mrow;
+        sXm[S.sPcol[s2]] = pdep64(S.sUi[s2], J);
     }
     __syncwarp();
     for (int c = lane; c < 64; c += 32) {
-        st->zmap[c] = sZm[c];
+        st->zmap[c] = sXp[c];
         st->xmap[c] = sXm[c];
     }
-    for (int s = lane; s < t; s += 32) {
-        st->prow[s] = sProw[s];
-        st->zpiv[s] = sZp[s] ^ (1ull << s);
-        st->newblk[s] = sUw[s] | pdep64(sXp[s], J);
+    for (int s2 = lane; s2 < t; s2 += 32) {
+        st->prow[s2] = S.Wph[s2];
+        st->pcol[s2] = S.sPcol[s2];
+        st->newblk[s2] = S.sNew[s2];
+        st->zpiv[s2] = S.sLi[s2];
     }
     if (lane == 0) {
         st->r_cur = r;
@@ -336,17 +621,19 @@ k_pivot(const u64 *__restrict__ side, int *__restrict__ perm, PanelState *st, in
 // Table sweep of panel b (MakeTable1 + AddRowsFromTable).
 //
 // For a row at position p >= r+kbar with raw panel word w:
-//   z       = coordinates of w over the original pivot words O (8 lookups in
-//             the byte tables ZT built from zmap),
-//   panel   = its multipliers scattered to the pivot columns (byte tables XT),
-//   trailing words ^= z.O (8 lookups, one Gray-code table per 8 pivots).
+//   z       = its coordinates over the original pivot rows O (eight byte
+//             lookups into tables built from zmap),
+//   panel   <- its multipliers scattered to the pivot columns (tables from xmap),
+//   trailing words ^= z.O (eight 128-bit lookups, one Gray-code table of 256
+//             sums per 8 pivots: MakeTable over the rows of O).
 // Pivot row t gets its final row U_t = zpiv[t].O, written to `out` at its
-// final position (pivot rows are never modified in A, so the tables can be
-// built from A while the sweep runs). The CTA holding word b+1 also stores it
-// in the next panel's side buffer.
+// final position; pivot rows are never written in A, so the tables can be built
+// from A while the sweep runs. The CTA holding word b+1 also stores it in the
+// next panel's side buffer.
 //
-// Work: column tiles of TW words (from the even word <= b) x row chunks; a
-// CTA keeps its tables while consecutive work items share a tile.
+// Work: column tiles of TW words (from the even word <= b) x row chunks; a CTA
+// keeps its tables while consecutive work items share a tile, and keeps RPT
+// rows per thread in flight.
 // ---------------------------------------------------------------------------
 template <int TW, int RPT, int MINB>
 __global__ void __launch_bounds__(256, MINB)
@@ -358,7 +645,7 @@ k_sweep(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_c
     constexpr int RPP = 256 / TPR;  // rows per thread slot and pass
     constexpr int BPL = 8 / TPR;    // z-table bytes per thread
     extern __shared__ __align__(16) u64 sm[];
-    u64 *sT = sm;                 // [8][256][TW]  Gray-code tables of the pivot rows
+    u64 *sT = sm;                 // [8][256][TW]  Gray-code tables of the pivot rows O
     u64 *sZ = sT + 8 * 256 * TW;  // [8][256]      raw panel byte -> coordinates z
     u64 *sX = sZ + 8 * 256;       // [8][256]      raw panel byte -> new panel word
     u64 *sO = sX + 8 * 256;       // [64][TW]      pivot rows, current tile
@@ -417,10 +704,10 @@ k_sweep(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_c
         if (tile != cur_tile) {
             __syncthreads();
             for (int e = tid; e < 64 * TW; e += 256) {
-                const int s = e / TW, wi = e % TW;
+                const int s2 = e / TW, wi = e % TW;
                 u64 v = 0;
-                if (s < kbar && wbase + wi < W)
-                    v = A[(int64_t)st->prow[s] * stride + wbase + wi];
+                if (s2 < kbar && wbase + wi < W)
+                    v = A[(int64_t)st->prow[s2] * stride + wbase + wi];
                 sO[e] = v;
             }
             __syncthreads();
