@@ -73,6 +73,7 @@ static size_t q_scratch_offset(const ElimLayout &L, int64_t n)
 }
 
 int identity_fill(int64_t *P, int64_t m, int64_t *Q, int64_t n, int64_t *rank, cudaStream_t s);
+int identity_perm(int *perm, int64_t m, cudaStream_t s);
 
 // internal workspace, one per device, grown on demand
 struct InternalWork {
@@ -147,6 +148,8 @@ static int check_opts(const gf2_opts *o)
         return GF2_EINVAL;
     if (o->grid_ctas < 0 || o->product < 0 || o->product > 2 || o->cutoff_cols < 0)
         return GF2_EINVAL;
+    if (o->cutoff_cols != 0 && o->cutoff_cols < 128)
+        return GF2_EINVAL;
     for (int i = 0; i < 8; ++i)
         if (o->reserved[i])
             return GF2_EINVAL;
@@ -176,6 +179,21 @@ static Elim make_elim(uint64_t *A, int64_t m, int64_t n, int64_t stride, char *w
     return e;
 }
 
+// Panel elimination (MMPF) of one view: the base case of the recursive PLS.
+// perm_out receives the position -> view row map of the result.
+int pls_base(uint64_t *A, int64_t stride, int64_t m, int64_t n, int64_t *P, int64_t *Q, int *perm_out, int64_t *rank,
+             char *work, const gf2_opts *opts, cudaStream_t s)
+{
+    if (m == 0 || n == 0)  // empty view: rank 0, identity P and Q, rows in place
+        return identity_fill(P, m, Q, n, rank, s) || identity_perm(perm_out, m, s) ? GF2_ECUDA : GF2_OK;
+    const ElimLayout L = elim_layout(GF2_OP_PLS, m, n);
+    Elim e = make_elim(A, m, n, stride, work, L, P, Q, true, opts, s);
+    int rc;
+    if ((rc = elim_run(e)) || (rc = elim_gather(e, rank)) || (rc = pls_finish(e)))
+        return rc;
+    return note_cuda(cudaMemcpyAsync(perm_out, e.perm, (size_t)m * sizeof(int), cudaMemcpyDeviceToDevice, s));
+}
+
 }  // namespace gf2
 
 using namespace gf2;
@@ -188,6 +206,9 @@ size_t gf2_workspace_bytes(int op, int64_t m, int64_t n, const gf2_opts *opts)
         return 0;
     switch (op) {
     case GF2_OP_PLS:
+        if (opts && opts->cutoff_cols > 0 && n > opts->cutoff_cols)
+            return rec_workspace_bytes(m, n, opts->cutoff_cols);
+        return elim_layout(op, m, n).total;
     case GF2_OP_RREF:
     case GF2_OP_RANK:
         return elim_layout(op, m, n).total;
@@ -211,6 +232,12 @@ int gf2_pls(uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *P, int64
     cudaStream_t s = (cudaStream_t)stream;
     if (m == 0 || n == 0)
         return identity_fill(P, m, Q, n, rank, s);
+    if (opts && opts->cutoff_cols > 0 && n > opts->cutoff_cols) {
+        // recursive PLS (Sec. 5) down to the MMPF base case at the cutoff (Sec. 6)
+        if ((rc = get_work(work, work_bytes, rec_workspace_bytes(m, n, opts->cutoff_cols))))
+            return rc;
+        return pls_recursive(A, stride, m, n, P, Q, rank, (char *)work, opts, s);
+    }
     const ElimLayout L = elim_layout(GF2_OP_PLS, m, n);
     if ((rc = get_work(work, work_bytes, L.total)))
         return rc;

@@ -31,9 +31,10 @@ __global__ void k_init(const uint64_t *__restrict__ A, int64_t stride, int *__re
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m) {
         perm[i] = i;
-        side0[i] = A[(int64_t)i * stride];
+        if (side0)
+            side0[i] = A[(int64_t)i * stride];
     }
-    if (i == 0) {
+    if (i == 0 && st) {
         st->r_cur = 0;
         st->r_next = 0;
         st->kbar = 0;
@@ -981,6 +982,15 @@ int launch_sweep(const gf2::Elim &e, int b)
 }  // namespace
 
 namespace gf2 {
+
+int identity_perm(int *perm, int64_t m, cudaStream_t s)
+{
+    if (m <= 0)
+        return GF2_OK;
+    k_init<<<(int)((m + 255) / 256), 256, 0, s>>>(nullptr, 0, perm, nullptr, nullptr, (int)m);
+    prof_launched(1);
+    return note_cuda(cudaGetLastError());
+}
 
 int identity_fill(int64_t *P, int64_t m, int64_t *Q, int64_t n, int64_t *rank, cudaStream_t s)
 {

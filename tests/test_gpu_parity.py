@@ -161,3 +161,22 @@ def test_device_generator_matches_host(g):
         assert (host(D) == S.bernoulli(m, n, 0.01, 7)).all()
         synth_gpu.fill(D, n, 8, p=0.3, echelon_frac=0.5)
         assert (host(D) == S.echelon(m, n, 0.3, 8)).all()
+
+
+@pytest.mark.parametrize("cutoff", [128, 256, 512])
+def test_recursive_pls_parity(g, cutoff):
+    """Recursive PLS (split, row gathers, lower solve, product, second call, merge)
+    down to the panel elimination at the cutoff: identical to the Gaussian PLS."""
+    shapes = [(300, 1000), (1000, 700), (640, 640), (257, 1300), (1500, 2000)]
+    for i, (m, n) in enumerate(shapes):
+        for kind in ("dense", "lowrank", "sparse05", "echelon", "deep", "zero"):
+            A = make(kind, m, n, 900 + 13 * i + cutoff)
+            check_pls(g, A, m, n, opts={"cutoff_cols": cutoff})
+
+
+def test_recursive_pls_user_workspace(g):
+    m, n = 1100, 1500
+    opts = {"cutoff_cols": 256}
+    work = g.new_workspace(g.OP_PLS, m, n, opts=opts)
+    for seed in (1, 2):
+        check_pls(g, S.dense(m, n, seed), m, n, opts=opts, work=work)
