@@ -59,6 +59,7 @@ extern "C" {
 #define GF2_ENOSPACE 5 /* work_bytes smaller than gf2_workspace_bytes() */
 #define GF2_EDIM 6     /* mismatched dimensions (gf2_mul) */
 #define GF2_ETOOBIG 7  /* matrix too large for the fixed scratch of gf2_rank_noalloc */
+#define GF2_ETIMEOUT 8 /* a device-side wait gave up (reported by gf2_sync_status) */
 
 /* op codes for gf2_workspace_bytes */
 #define GF2_OP_PLS 1
@@ -142,6 +143,36 @@ int gf2_mul(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64
             const gf2_opts *opts, void *stream);
 
 /*
+ * Batched PLS: many independent matrices in one call (the paper decomposes one
+ * matrix at a time; the batch runs the same MMPF block elimination, Sec. 4.1,
+ * on every matrix at once, so that step b -- the pivot search and the table
+ * sweep of panel b -- is one launch over all matrices that have a panel b).
+ * Each matrix's results are bit for bit those of gf2_pls on it alone without
+ * the recursive split (opts->cutoff_cols is ignored).
+ *   items  -- HOST array of `count` descriptors; the pointers inside are device
+ *             pointers (A in/out, P and Q out, as for gf2_pls). Matrices and
+ *             their P, Q must not overlap one another;
+ *   ranks  -- device int64[count], out: ranks[i] = rank of matrix i;
+ *   work   -- device, gf2_pls_batched_workspace_bytes(items, count, opts)
+ *             bytes (which reads only the sizes m, n, stride of the items and
+ *             returns 0 for invalid ones), or NULL for the library's internal
+ *             workspace.
+ * Sizes are read on the host (the schedule of launches depends on them).
+ * count == 0 returns GF2_OK. Items with m == 0 or n == 0 get rank 0 and
+ * identity P, Q.
+ */
+typedef struct {
+    uint64_t *A;    /* device, m x n, stride words per row */
+    int64_t m, n, stride;
+    int64_t *P;     /* device int64, length m */
+    int64_t *Q;     /* device int64, length n */
+} gf2_batch_item;
+
+size_t gf2_pls_batched_workspace_bytes(const gf2_batch_item *items, int64_t count, const gf2_opts *opts);
+int gf2_pls_batched(const gf2_batch_item *items, int64_t count, int64_t *ranks, void *work, size_t work_bytes,
+                    const gf2_opts *opts, void *stream);
+
+/*
  * Rank without allocating device memory. The paper has no counterpart: this
  * entry point exists for callers that may not call cudaMalloc -- code that runs
  * while a CUDA graph is being captured, loops that cannot afford the device
@@ -164,6 +195,24 @@ int gf2_mul(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64
  */
 #define GF2_NOALLOC_SCRATCH_BYTES (4u << 20)
 int gf2_rank_noalloc(const uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *rank, void *stream);
+
+/*
+ * Device-side errors. Kernels that wait on the tensor cores or on a flag give
+ * up after a bounded time (2 s) instead of spinning forever; they then record
+ * GF2_ETIMEOUT in a per-device status word and finish without writing their
+ * outputs. gf2_sync_status waits for `stream` (host-blocking), returns the
+ * recorded code (GF2_OK if none) and clears it. The word is per device and
+ * sticky: an error from any stream stays until it is read.
+ */
+int gf2_sync_status(void *stream);
+
+/*
+ * Diagnostic for the path above (not part of the method): launches one kernel
+ * that waits on a device flag nothing ever sets, with the wait limited to
+ * limit_ns nanoseconds (capped at the library's 2 s limit). It returns as soon
+ * as the launch is enqueued; a following gf2_sync_status reports GF2_ETIMEOUT.
+ */
+int gf2_diag_wait_timeout(uint64_t limit_ns, void *stream);
 
 /* Human-readable text for a GF2_* code (static storage). */
 const char *gf2_strerror(int code);

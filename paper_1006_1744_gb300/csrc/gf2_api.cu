@@ -83,7 +83,7 @@ struct InternalWork {
 };
 static InternalWork g_work;
 
-static int get_work(void *&work, size_t &work_bytes, size_t need)
+int get_work(void *&work, size_t &work_bytes, size_t need)
 {
     if (work) {
         if ((uintptr_t)work % 256)
@@ -120,7 +120,7 @@ static int get_work(void *&work, size_t &work_bytes, size_t need)
     return GF2_OK;
 }
 
-static int check_mat(const void *A, int64_t m, int64_t n, int64_t stride)
+int check_mat(const void *A, int64_t m, int64_t n, int64_t stride)
 {
     if (m < 0 || n < 0 || m > INT32_MAX - 64 || n > INT32_MAX - 64)
         return GF2_EINVAL;
@@ -138,7 +138,7 @@ static int check_mat(const void *A, int64_t m, int64_t n, int64_t stride)
     return GF2_OK;
 }
 
-static int check_opts(const gf2_opts *o)
+int check_opts(const gf2_opts *o)
 {
     if (!o)
         return GF2_OK;
@@ -213,7 +213,7 @@ size_t gf2_workspace_bytes(int op, int64_t m, int64_t n, const gf2_opts *opts)
     case GF2_OP_RANK:
         return elim_layout(op, m, n).total;
     case GF2_OP_MUL:
-        return align_up(mul_tensor_workspace(m, 0, n) + 256, 256);
+        return align_up(mul_tensor_workspace(m, 0, n), 256);
     default:
         return 0;
     }
@@ -352,6 +352,8 @@ const char *gf2_strerror(int code)
         return "mismatched dimensions";
     case GF2_ETOOBIG:
         return "matrix too large for the fixed scratch of gf2_rank_noalloc (GF2_NOALLOC_SCRATCH_BYTES)";
+    case GF2_ETIMEOUT:
+        return "a device-side wait gave up (bounded wait expired)";
     default:
         return "unknown error";
     }

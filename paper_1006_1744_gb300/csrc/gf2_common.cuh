@@ -79,9 +79,36 @@ __device__ __forceinline__ u64 pdep64(u64 x, u64 m)
 }
 
 // ---------------------------------------------------------------------------
+// bounded waits and the device status word
+// ---------------------------------------------------------------------------
+// Every spin-wait in the library gives up after this long, records
+// GF2_ETIMEOUT in the status word and lets its kernel finish.
+#define GF2_WAIT_LIMIT_NS 2000000000ull
+
+__device__ __forceinline__ u64 globaltimer_ns()
+{
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// first error wins; later ones leave it in place until gf2_sync_status clears it
+__device__ __forceinline__ void record_status(int *status, int code)
+{
+    if (status)
+        atomicCAS(status, 0, code);
+}
+
+// ---------------------------------------------------------------------------
 // host helpers
 // ---------------------------------------------------------------------------
 namespace gf2 {
+
+int *status_word();  // device address of this device's status word (nullptr on failure)
+// argument checks and the internal per-device workspace (gf2_api.cu)
+int get_work(void *&work, size_t &work_bytes, size_t need);  // caller's work if given, else the internal one
+int check_mat(const void *A, int64_t m, int64_t n, int64_t stride);
+int check_opts(const gf2_opts *o);
 
 int note_cuda(cudaError_t e);  // records e for gf2_last_cuda_error, returns GF2_ECUDA or GF2_OK
 void prof_launched(int count);              // counts kernel launches when profiling is on
@@ -118,6 +145,31 @@ struct Elim {
     cudaStream_t s;
     int tile_words, grid;
 };
+
+// One matrix of a batched elimination (device-resident array, one per matrix).
+struct ElimDesc {
+    uint64_t *A;
+    int64_t stride;
+    PanelState *st;
+    int *perm;
+    u64 *side;
+    u64 *pmask;
+    uint64_t *out;
+    int64_t ostride;
+    int64_t *P, *Q, *rank;
+    int m, n, W, pad;
+};
+
+// Batched panel elimination (gf2_pls.cu). Step b runs panel b of the nact
+// matrices idx[0..nact) in two launches; the sweep's CTAs are split among them
+// by the prefix pre[0..nact] (matrix idx[j] gets CTAs pre[j]..pre[j+1]-1).
+int batch_init(const ElimDesc *D, int count, int max_m, cudaStream_t s);
+int batch_pivot(const ElimDesc *D, const int *idx, int nact, int b, cudaStream_t s);
+int batch_sweep(const ElimDesc *D, const int *idx, const int *pre, int nact, int total, int b, int tile_words,
+                cudaStream_t s);
+int batch_finish(const ElimDesc *D, int count, int max_m, cudaStream_t s);
+int sweep_rows_per_pass(int tile_words);
+int sweep_ctas_per_sm(int tile_words);
 
 // panel elimination: runs every panel; afterwards st->r_next is the rank.
 int elim_run(const Elim &e);

@@ -539,9 +539,8 @@ __device__ void pivot_rows(const u64 *__restrict__ side, int *__restrict__ perm,
     J_out = J;
 }
 
-__global__ void __launch_bounds__(32, 1)
-k_pivot(const u64 *__restrict__ side, int *__restrict__ perm, PanelState *st, int64_t *P,
-        int64_t *Q, int m, int b, int nbits)
+__device__ __forceinline__ void pivot_panel(const u64 *__restrict__ side, int *__restrict__ perm, PanelState *st,
+                                            int64_t *P, int64_t *Q, int m, int b, int nbits)
 {
     __shared__ PivotShared S;
     __shared__ u64 sXp[64], sXm[64];
@@ -618,6 +617,13 @@ k_pivot(const u64 *__restrict__ side, int *__restrict__ perm, PanelState *st, in
     }
 }
 
+__global__ void __launch_bounds__(32, 1)
+k_pivot(const u64 *__restrict__ side, int *__restrict__ perm, PanelState *st, int64_t *P, int64_t *Q, int m,
+        int b, int nbits)
+{
+    pivot_panel(side, perm, st, P, Q, m, b, nbits);
+}
+
 // ---------------------------------------------------------------------------
 // Table sweep of panel b (MakeTable1 + AddRowsFromTable).
 //
@@ -636,11 +642,11 @@ k_pivot(const u64 *__restrict__ side, int *__restrict__ perm, PanelState *st, in
 // keeps its tables while consecutive work items share a tile, and keeps RPT
 // rows per thread in flight.
 // ---------------------------------------------------------------------------
-template <int TW, int RPT, int MINB>
-__global__ void __launch_bounds__(256, MINB)
-k_sweep(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_cur,
-        u64 *__restrict__ side_nxt, const int *__restrict__ perm, const PanelState *__restrict__ st,
-        uint64_t *__restrict__ out, int64_t ostride, int m, int W, int b)
+template <int TW, int RPT>
+__device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_cur,
+                                            u64 *__restrict__ side_nxt, const int *__restrict__ perm,
+                                            const PanelState *__restrict__ st, uint64_t *__restrict__ out,
+                                            int64_t ostride, int m, int W, int b, int cta, int ncta)
 {
     constexpr int TPR = TW / 2;     // threads per row, two words each
     constexpr int RPP = 256 / TPR;  // rows per thread slot and pass
@@ -659,7 +665,7 @@ k_sweep(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_c
     const int tid = threadIdx.x;
     if (kbar == 0) {
         if (b + 1 < W)
-            for (int p = r + blockIdx.x * 256 + tid; p < m; p += gridDim.x * 256) {
+            for (int p = r + cta * 256 + tid; p < m; p += ncta * 256) {
                 int ph = perm[p];
                 side_nxt[ph] = A[(int64_t)ph * stride + b + 1];
             }
@@ -668,7 +674,7 @@ k_sweep(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_c
     const int wstart = b & ~1;
     const int tiles = (W - wstart + TW - 1) / TW;
     constexpr int PASS = RPP * RPT;  // rows per pass of the CTA
-    int chunks = gridDim.x / tiles;
+    int chunks = ncta / tiles;
     if (chunks < 1)
         chunks = 1;
     int R = (M + chunks - 1) / chunks;
@@ -699,7 +705,7 @@ k_sweep(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_c
     // lanes of one row form an aligned group of TPR lanes
     const unsigned gmask = (TPR == 32 ? GF2_FULL : ((1u << TPR) - 1u) << (lane & ~(TPR - 1)));
     int cur_tile = -1;
-    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    for (int item = cta; item < items; item += ncta) {
         const int tile = item / chunks, chunk = item % chunks;
         const int wbase = wstart + tile * TW;
         if (tile != cur_tile) {
@@ -834,19 +840,29 @@ k_sweep(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_c
     }
 }
 
+template <int TW, int RPT, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+k_sweep(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_cur, u64 *__restrict__ side_nxt,
+        const int *__restrict__ perm, const PanelState *__restrict__ st, uint64_t *__restrict__ out,
+        int64_t ostride, int m, int W, int b)
+{
+    sweep_panel<TW, RPT>(A, stride, side_cur, side_nxt, perm, st, out, ostride, m, W, b, blockIdx.x, gridDim.x);
+}
+
 // ---------------------------------------------------------------------------
 // final row order: out[p] <- A[perm[p]] for the words the sweep did not write
 // (all words for p >= r, the words left of the pivot's panel for p < r),
 // identity fill of P and Q beyond the rank, rank.
 // ---------------------------------------------------------------------------
-__global__ void k_gather(const uint64_t *__restrict__ A, int64_t stride, const int *__restrict__ perm,
-                         const PanelState *__restrict__ st, int64_t *__restrict__ P,
-                         int64_t *__restrict__ Q, uint64_t *__restrict__ out, int64_t ostride, int m,
-                         int n, int W, int64_t *rank)
+__device__ __forceinline__ void gather_rows(const uint64_t *__restrict__ A, int64_t stride,
+                                            const int *__restrict__ perm, const PanelState *__restrict__ st,
+                                            int64_t *__restrict__ P, int64_t *__restrict__ Q,
+                                            uint64_t *__restrict__ out, int64_t ostride, int m, int n, int W,
+                                            int64_t *rank, int cta, int ncta)
 {
     const int r = st->r_next;
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int warps = ncta * (blockDim.x >> 5);
+    const int wid = cta * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (out) {
         for (int p = wid; p < m; p += warps) {
@@ -858,8 +874,8 @@ __global__ void k_gather(const uint64_t *__restrict__ A, int64_t stride, const i
                 dst[w] = src[w];
         }
     }
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nt = gridDim.x * blockDim.x;
+    const int g = cta * blockDim.x + threadIdx.x;
+    const int nt = ncta * blockDim.x;
     if (P)
         for (int i = r + g; i < m; i += nt)
             P[i] = i;
@@ -870,24 +886,36 @@ __global__ void k_gather(const uint64_t *__restrict__ A, int64_t stride, const i
         *rank = r;
 }
 
-__global__ void k_pmask(const int64_t *__restrict__ Q, const PanelState *__restrict__ st,
-                        u64 *__restrict__ pmask)
+__global__ void k_gather(const uint64_t *__restrict__ A, int64_t stride, const int *__restrict__ perm,
+                         const PanelState *__restrict__ st, int64_t *__restrict__ P, int64_t *__restrict__ Q,
+                         uint64_t *__restrict__ out, int64_t ostride, int m, int n, int W, int64_t *rank)
+{
+    gather_rows(A, stride, perm, st, P, Q, out, ostride, m, n, W, rank, blockIdx.x, gridDim.x);
+}
+
+__device__ __forceinline__ void pivot_mask(const int64_t *__restrict__ Q, const PanelState *__restrict__ st,
+                                           u64 *__restrict__ pmask, int cta, int ncta)
 {
     const int r = st->r_next;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < r; s += gridDim.x * blockDim.x) {
+    for (int s = cta * blockDim.x + threadIdx.x; s < r; s += ncta * blockDim.x) {
         const int64_t c = Q[s];
         atomicOr(&pmask[c >> 6], 1ull << (c & 63));
     }
+}
+
+__global__ void k_pmask(const int64_t *__restrict__ Q, const PanelState *__restrict__ st, u64 *__restrict__ pmask)
+{
+    pivot_mask(Q, st, pmask, blockIdx.x, gridDim.x);
 }
 
 // Compress L: row i (t = min(i, r-1)) gets the bits of columns Q[c0..t] at
 // positions c0..t, zeros up to Q[t], the rest unchanged (c0 = first s with
 // Q[s] != s). This is the effect of swapping columns j and Q[j] from row j on
 // for j = 0..r-1, done as one ordered bit extraction per row.
-__global__ void k_compress(uint64_t *__restrict__ out, int64_t stride, const int64_t *__restrict__ Q,
-                           const u64 *__restrict__ pmask, const PanelState *__restrict__ st, int m)
+__device__ __forceinline__ void compress_row(uint64_t *__restrict__ out, int64_t stride,
+                                             const int64_t *__restrict__ Q, const u64 *__restrict__ pmask,
+                                             const PanelState *__restrict__ st, int m, int i)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = st->r_next;
     if (i >= m || r == 0)
         return;
@@ -937,6 +965,12 @@ __global__ void k_compress(uint64_t *__restrict__ out, int64_t stride, const int
     }
 }
 
+__global__ void k_compress(uint64_t *__restrict__ out, int64_t stride, const int64_t *__restrict__ Q,
+                           const u64 *__restrict__ pmask, const PanelState *__restrict__ st, int m)
+{
+    compress_row(out, stride, Q, pmask, st, m, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 __global__ void k_identity(int64_t *P, int64_t m, int64_t *Q, int64_t n, int64_t *rank)
 {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -979,9 +1013,159 @@ int launch_sweep(const gf2::Elim &e, int b)
     return gf2::note_cuda(cudaGetLastError());
 }
 
+// ---------------------------------------------------------------------------
+// batched elimination: the same panel steps over many matrices per launch
+// ---------------------------------------------------------------------------
+__global__ void k_init_b(const gf2::ElimDesc *__restrict__ D)
+{
+    const gf2::ElimDesc d = D[blockIdx.y];
+    const int g = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    for (int i = g; i < d.m; i += nt) {
+        d.perm[i] = i;
+        if (d.W > 0)
+            d.side[i] = d.A[(int64_t)i * d.stride];
+    }
+    for (int w = g; w < d.W + 1; w += nt)
+        d.pmask[w] = 0;
+    if (g == 0) {
+        d.st->r_cur = 0;
+        d.st->r_next = 0;
+        d.st->kbar = 0;
+        d.st->status = 0;
+        d.st->zero_tail = 0;
+        d.st->J = 0;
+    }
+}
+
+__global__ void __launch_bounds__(32, 1) k_pivot_b(const gf2::ElimDesc *__restrict__ D, const int *__restrict__ idx, int b)
+{
+    const gf2::ElimDesc &d = D[idx[blockIdx.x]];
+    const int nbits = min(64, d.n - 64 * b);
+    pivot_panel(d.side + (size_t)(b & 1) * d.m, d.perm, d.st, d.P, d.Q, d.m, b, nbits);
+}
+
+template <int TW, int RPT, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+k_sweep_b(const gf2::ElimDesc *__restrict__ D, const int *__restrict__ idx, const int *__restrict__ pre, int nact, int b)
+{
+    // matrix j with pre[j] <= blockIdx.x < pre[j + 1]
+    int lo = 0, hi = nact - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= (int)blockIdx.x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const gf2::ElimDesc &d = D[idx[lo]];
+    sweep_panel<TW, RPT>(d.A, d.stride, d.side + (size_t)(b & 1) * d.m, d.side + (size_t)((b + 1) & 1) * d.m, d.perm,
+                         d.st, d.out, d.ostride, d.m, d.W, b, (int)blockIdx.x - pre[lo], pre[lo + 1] - pre[lo]);
+}
+
+__global__ void k_gather_b(const gf2::ElimDesc *__restrict__ D)
+{
+    const gf2::ElimDesc &d = D[blockIdx.y];
+    gather_rows(d.A, d.stride, d.perm, d.st, d.P, d.Q, d.out, d.ostride, d.m, d.n, d.W, d.rank, blockIdx.x,
+                gridDim.x);
+}
+
+__global__ void k_pmask_b(const gf2::ElimDesc *__restrict__ D)
+{
+    const gf2::ElimDesc &d = D[blockIdx.y];
+    pivot_mask(d.Q, d.st, d.pmask, blockIdx.x, gridDim.x);
+}
+
+__global__ void k_compress_b(const gf2::ElimDesc *__restrict__ D)
+{
+    const gf2::ElimDesc &d = D[blockIdx.y];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < d.m)
+        compress_row(d.out, d.ostride, d.Q, d.pmask, d.st, d.m, i);
+}
+
+// out -> A, one warp per row
+__global__ void k_copyback_b(const gf2::ElimDesc *__restrict__ D)
+{
+    const gf2::ElimDesc &d = D[blockIdx.y];
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    const int lane = threadIdx.x & 31;
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < d.m; i += warps) {
+        const uint64_t *src = d.out + (int64_t)i * d.ostride;
+        uint64_t *dst = d.A + (int64_t)i * d.stride;
+        for (int w = lane; w < d.W; w += 32)
+            dst[w] = src[w];
+    }
+}
+
 }  // namespace
 
 namespace gf2 {
+
+int sweep_rows_per_pass(int tile_words) { return tile_words == 4 ? (256 / 2) * 4 : (256 / 4) * 4; }
+int sweep_ctas_per_sm(int tile_words) { return tile_words == 4 ? 2 : 1; }
+
+int batch_init(const ElimDesc *D, int count, int max_m, cudaStream_t s)
+{
+    if (count <= 0)
+        return GF2_OK;
+    const dim3 grid((unsigned)((max_m + 255) / 256 > 0 ? (max_m + 255) / 256 : 1), (unsigned)count);
+    k_init_b<<<grid, 256, 0, s>>>(D);
+    prof_launched(1);
+    return note_cuda(cudaGetLastError());
+}
+
+int batch_pivot(const ElimDesc *D, const int *idx, int nact, int b, cudaStream_t s)
+{
+    if (nact <= 0)
+        return GF2_OK;
+    const int tok = prof_begin(s);
+    k_pivot_b<<<nact, 32, 0, s>>>(D, idx, b);
+    prof_end(s, GF2_PROF_PIVOT, tok);
+    prof_launched(1);
+    return note_cuda(cudaGetLastError());
+}
+
+template <int TW, int RPT, int MINB>
+static int launch_sweep_b(const ElimDesc *D, const int *idx, const int *pre, int nact, int total, int b,
+                          cudaStream_t s)
+{
+    static bool attr_set = false;
+    constexpr size_t smem = sweep_smem<TW>();
+    if (!attr_set) {
+        cudaError_t err =
+            cudaFuncSetAttribute(k_sweep_b<TW, RPT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess)
+            return note_cuda(err);
+        attr_set = true;
+    }
+    const int tok = prof_begin(s);
+    k_sweep_b<TW, RPT, MINB><<<total, 256, smem, s>>>(D, idx, pre, nact, b);
+    prof_end(s, GF2_PROF_SWEEP, tok);
+    prof_launched(1);
+    return note_cuda(cudaGetLastError());
+}
+
+int batch_sweep(const ElimDesc *D, const int *idx, const int *pre, int nact, int total, int b, int tile_words,
+                cudaStream_t s)
+{
+    if (nact <= 0 || total <= 0)
+        return GF2_OK;
+    return tile_words == 4 ? launch_sweep_b<4, 4, 2>(D, idx, pre, nact, total, b, s)
+                           : launch_sweep_b<8, 4, 1>(D, idx, pre, nact, total, b, s);
+}
+
+int batch_finish(const ElimDesc *D, int count, int max_m, cudaStream_t s)
+{
+    if (count <= 0)
+        return GF2_OK;
+    const unsigned gx = (unsigned)((max_m + 127) / 128 > 0 ? (max_m + 127) / 128 : 1);
+    k_gather_b<<<dim3(gx < 8 ? gx : 8, (unsigned)count), 256, 0, s>>>(D);
+    k_pmask_b<<<dim3(1, (unsigned)count), 256, 0, s>>>(D);
+    k_compress_b<<<dim3(gx, (unsigned)count), 128, 0, s>>>(D);
+    k_copyback_b<<<dim3(gx < 16 ? gx : 16, (unsigned)count), 256, 0, s>>>(D);
+    prof_launched(4);
+    return note_cuda(cudaGetLastError());
+}
 
 int identity_perm(int *perm, int64_t m, cudaStream_t s)
 {

@@ -43,6 +43,10 @@ class Opts(ctypes.Structure):
                 ("cutoff_cols", _i64), ("reserved", _int * 8)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("A", _vp), ("m", _i64), ("n", _i64), ("stride", _i64), ("P", _vp), ("Q", _vp)]
+
+
 SYMBOLS = {
     "gf2_workspace_bytes": (_sz, [_int, _i64, _i64, _vp]),
     "gf2_pls": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),
@@ -53,6 +57,10 @@ SYMBOLS = {
     "gf2_last_cuda_error": (_int, []),
     "gf2_version": (_int, []),
     "gf2_rank_noalloc": (_int, [_vp, _i64, _i64, _i64, _vp, _vp]),
+    "gf2_pls_batched_workspace_bytes": (_sz, [_vp, _i64, _vp]),
+    "gf2_pls_batched": (_int, [_vp, _i64, _vp, _vp, _sz, _vp, _vp]),
+    "gf2_sync_status": (_int, [_vp]),
+    "gf2_diag_wait_timeout": (_int, [ctypes.c_uint64, _vp]),
     "gf2_prof_enable": (None, [_int]),
     "gf2_prof_reset": (None, []),
     "gf2_prof_launches": (ctypes.c_longlong, []),
@@ -136,6 +144,8 @@ def _check(code, what):
 def _mat(A, n, what):
     if A.dtype != torch.int64 or A.dim() != 2 or not A.is_cuda:
         raise ValueError(f"{what}: expected a 2-D torch.int64 CUDA tensor (packed rows)")
+    if A.numel() == 0:
+        return A.shape[0], max(int(A.shape[1]), 16)
     if A.stride(1) != 1:
         raise ValueError(f"{what}: rows must be contiguous")
     return A.shape[0], A.stride(0)
@@ -213,3 +223,46 @@ def mul(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, m: int, k: int, n: in
     _check(lib().gf2_mul(_ptr(C), sc, _ptr(A), sa, _ptr(B), sb, m, k, n, int(bool(accumulate)), wp, wb,
                          _opts(opts), _stream(stream)), "gf2_mul")
     return C
+
+
+def sync_status(stream=None) -> int:
+    """Waits for the stream; returns and clears the device status word (0 = ok)."""
+    return int(lib().gf2_sync_status(_stream(stream)))
+
+
+def diag_wait_timeout(limit_ns: int, stream=None) -> None:
+    """Launches a kernel whose bounded wait on a never-set flag runs out."""
+    _check(lib().gf2_diag_wait_timeout(int(limit_ns), _stream(stream)), "gf2_diag_wait_timeout")
+
+
+def batch_items(mats, ns, Ps, Qs):
+    """Host array of gf2_batch_item for device tensors (A_i of shape (m_i, stride_i))."""
+    arr = (BatchItem * max(1, len(mats)))()
+    for i, (A, n, P, Q) in enumerate(zip(mats, ns, Ps, Qs)):
+        m, stride = _mat(A, n, "gf2_pls_batched")
+        arr[i] = BatchItem(_ptr(A), m, n, stride, _ptr(P), _ptr(Q))
+    return arr
+
+
+def pls_batched_workspace_bytes(shapes, opts=None) -> int:
+    """Workspace bytes for matrices of the given (m, n, stride) shapes."""
+    items = (BatchItem * max(1, len(shapes)))()
+    for i, (m, n, stride) in enumerate(shapes):
+        items[i] = BatchItem(None, m, n, stride, None, None)
+    return int(lib().gf2_pls_batched_workspace_bytes(items, len(shapes), _opts(opts)))
+
+
+def pls_batched(mats, ns, Ps=None, Qs=None, ranks=None, work=None, opts=None, stream=None):
+    """PLS of every matrix in `mats` (in place) in one batched call.
+    Returns (Ps, Qs, ranks) with ranks a device int64 tensor of length len(mats)."""
+    dev = mats[0].device if mats else torch.device("cuda")
+    if Ps is None:
+        Ps = [torch.empty(max(1, int(A.shape[0])), dtype=torch.int64, device=dev) for A in mats]
+    if Qs is None:
+        Qs = [torch.empty(max(1, int(n)), dtype=torch.int64, device=dev) for n in ns]
+    ranks = torch.empty(max(1, len(mats)), dtype=torch.int64, device=dev) if ranks is None else ranks
+    items = batch_items(mats, ns, Ps, Qs)
+    wp, wb = _work(work)
+    _check(lib().gf2_pls_batched(items, len(mats), _ptr(ranks), wp, wb, _opts(opts), _stream(stream)),
+           "gf2_pls_batched")
+    return Ps, Qs, ranks

@@ -150,3 +150,24 @@ def pack(B: np.ndarray, stride: int | None = None) -> np.ndarray:
     padded = padded.reshape(m, W, 64)
     out[:, :W] = np.bitwise_or.reduce(padded << np.arange(64, dtype=np.uint64)[None, None, :], axis=2)
     return out
+
+
+def _unit(seed: int, k: int) -> float:
+    """Uniform double in [0, 1) from counter k of ``seed`` (top 53 bits)."""
+    return float(int(mix(_U64(seed) ^ mix(_U64(k)))) >> 11) * (1.0 / 9007199254740992.0)
+
+
+def batch_recipe(count: int, base_seed: int):
+    """Shapes and densities of a batch of independent matrices (the many-matrix
+    workload): rows = floor(exp(U[ln 256, ln 8192])), cols = max(64, 64 *
+    round(rows * U[0.5, 2] / 64)), density drawn from {0.5, 0.1, 0.01}, seed of
+    matrix i = mix(base_seed + i). Returns a list of (m, n, p, seed)."""
+    out = []
+    lo, hi = np.log(256.0), np.log(8192.0)
+    for i in range(count):
+        s = int(mix(_U64((base_seed + i) & 0xFFFFFFFFFFFFFFFF)))
+        m = int(np.floor(np.exp(lo + (hi - lo) * _unit(s, 1))))
+        n = max(64, 64 * int(round(m * (0.5 + 1.5 * _unit(s, 2)) / 64)))
+        p = (0.5, 0.1, 0.01)[min(2, int(3 * _unit(s, 3)))]
+        out.append((m, n, p, s))
+    return out

@@ -97,3 +97,31 @@ def test_product_path_refuses_without_library(tmp_path, monkeypatch):
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         mod.lib()
     importlib.reload(g)
+
+
+def test_batched_workspace_and_checks_host_only(built):
+    """Batched PLS: workspace sizing reads only sizes; invalid items are refused
+    on the host before anything is enqueued."""
+    from paper_1006_1744_gb300 import gf2
+    one = gf2.pls_batched_workspace_bytes([(300, 700, 16)])
+    two = gf2.pls_batched_workspace_bytes([(300, 700, 16), (300, 700, 16)])
+    assert one >= gf2.workspace_bytes(gf2.OP_PLS, 300, 700)
+    assert two > one
+    assert gf2.pls_batched_workspace_bytes([]) > 0 or gf2.pls_batched_workspace_bytes([]) == 0
+    assert gf2.pls_batched_workspace_bytes([(10, 100, 1)]) == 0  # stride < ceil(n/64)
+    assert gf2.pls_batched_workspace_bytes([(-1, 5, 16)]) == 0
+    L = gf2.lib()
+    items = (gf2.BatchItem * 1)()
+    items[0] = gf2.BatchItem(None, 10, 10, 16, None, None)  # null A with m, n > 0
+    assert L.gf2_pls_batched(items, 1, None, None, 0, None, None) == 1
+    items[0] = gf2.BatchItem(0x1040, 10, 10, 16, 0x2000, 0x3000)  # A not 128-byte aligned
+    assert L.gf2_pls_batched(items, 1, None, None, 0, None, None) == 2
+    items[0] = gf2.BatchItem(0x1000, 10, 10, 16, None, 0x3000)  # P missing
+    assert L.gf2_pls_batched(items, 1, None, None, 0, None, None) == 1
+    assert L.gf2_pls_batched(items, -1, None, None, 0, None, None) == 1
+    assert L.gf2_pls_batched(None, 0, None, None, 0, None, None) == 0
+
+
+def test_status_codes_have_text(built):
+    from paper_1006_1744_gb300 import gf2
+    assert b"wait" in gf2.lib().gf2_strerror(8)

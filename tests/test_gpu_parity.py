@@ -180,3 +180,141 @@ def test_recursive_pls_user_workspace(g):
     work = g.new_workspace(g.OP_PLS, m, n, opts=opts)
     for seed in (1, 2):
         check_pls(g, S.dense(m, n, seed), m, n, opts=opts, work=work)
+
+
+TC = {"product": 2}
+MUL_SHAPES_TC = [(1, 1, 1), (64, 64, 64), (100, 130, 70), (513, 1000, 300), (1024, 1024, 1024),
+                 (2000, 65, 129), (37, 3000, 515), (129, 8300, 257), (300, 16500, 600)]
+
+
+@pytest.mark.parametrize("acc", [False, True])
+def test_mul_tensor_parity(g, acc):
+    """Tensor-core product (0/1 FP8 operands, FP32 sums, low bit) against the
+    oracle's product; inner dimensions past one accumulation segment (8192 bits)."""
+    rng = np.random.default_rng(11)
+    for (m, k, n) in MUL_SHAPES_TC:
+        A = S.dense(m, k, int(rng.integers(1 << 30)))
+        B = S.dense(k, n, int(rng.integers(1 << 30)))
+        C0 = S.dense(m, n, int(rng.integers(1 << 30)))
+        want = oracle.mul(A, B, m, k, n, C=C0 if acc else None, stride=C0.shape[1])
+        Cd = dev(C0)
+        g.mul(Cd, dev(A), dev(B), m, k, n, accumulate=acc, opts=TC)
+        torch.cuda.synchronize()
+        W = S.words_per_row(n)
+        assert (host(Cd)[:, :W] == want[:, :W]).all(), (m, k, n)
+    assert g.sync_status() == 0
+
+
+def test_mul_tensor_all_ones_sums(g):
+    """All-ones operands: every sum equals the inner dimension, so the parity of
+    each output bit is k mod 2 (the largest sums the accumulator sees)."""
+    for k in (31, 8191, 8192, 8193, 16383):
+        m, n = 130, 300
+        A = S.pack(np.ones((m, k), dtype=bool))
+        B = S.pack(np.ones((k, n), dtype=bool))
+        C = torch.zeros((m, S.default_stride(n)), dtype=torch.int64, device="cuda")
+        g.mul(C, dev(A), dev(B), m, k, n, opts=TC)
+        torch.cuda.synchronize()
+        want = S.pack(np.full((m, n), k & 1, dtype=bool))
+        assert (host(C) == want).all(), k
+
+
+def test_mul_tensor_views_with_foreign_bits(g):
+    """A, B and C as views inside wider matrices (the recursive PLS's A_SW, A_NE
+    and A_SE): bits of A past column k and of B past column n are other data and
+    must not leak in; C's words past its last column are not written."""
+    rng = np.random.default_rng(5)
+    for (m, k, n) in [(200, 100, 150), (300, 700, 333), (129, 64, 65)]:
+        Af = S.dense(m, k + 200, int(rng.integers(1 << 30)))
+        Bf = S.dense(k + 50, n + 300, int(rng.integers(1 << 30)))
+        Cf = S.dense(m, n + 300, int(rng.integers(1 << 30)))
+        Ak = S.pack(S.unpack(Af, m, k + 200)[:, :k])
+        Bk = S.pack(S.unpack(Bf, k + 50, n + 300)[:k, :n])
+        Ck = S.pack(S.unpack(Cf, m, n + 300)[:, :n])
+        want = S.unpack(oracle.mul(Ak, Bk, m, k, n, C=Ck, stride=Ck.shape[1]), m, n)
+        Cd = dev(Cf)
+        g.mul(Cd, dev(Af), dev(Bf)[:k], m, k, n, accumulate=True, opts=TC)
+        torch.cuda.synchronize()
+        got = S.unpack(host(Cd), m, n + 300)
+        assert (got[:, :n] == want).all()
+        assert (got[:, n:] == S.unpack(Cf, m, n + 300)[:, n:]).all()
+
+
+@pytest.mark.parametrize("cutoff", [128, 256])
+def test_recursive_pls_tensor_product_parity(g, cutoff):
+    """Recursive PLS with the tensor-core trailing product: identical to the
+    Gaussian PLS, like the XOR-table form."""
+    for i, (m, n) in enumerate([(300, 1000), (1000, 700), (1500, 2000)]):
+        for kind in ("dense", "lowrank", "sparse05", "echelon"):
+            A = make(kind, m, n, 1700 + 13 * i + cutoff)
+            check_pls(g, A, m, n, opts={"cutoff_cols": cutoff, "product": 2})
+    assert g.sync_status() == 0
+
+
+def test_bounded_wait_reports_timeout(g):
+    """A wait on a flag nothing sets gives up after its limit and records
+    GF2_ETIMEOUT; the context stays usable and the status clears on reading."""
+    assert g.sync_status() == 0
+    g.diag_wait_timeout(20_000_000)
+    assert g.sync_status() == 8
+    assert g.sync_status() == 0
+    A = S.dense(100, 100, 3)
+    check_pls(g, A, 100, 100)
+
+
+def test_pls_batched_parity(g):
+    """Batched PLS: every matrix of a mixed batch (shapes, densities, empty and
+    degenerate members) matches the oracle exactly, like gf2_pls on it alone."""
+    rng = np.random.default_rng(21)
+    shapes = [(0, 0), (0, 70), (50, 0), (1, 1), (64, 64), (300, 200), (129, 700), (700, 129),
+              (257, 257), (1000, 1500), (90, 64), (2000, 300)]
+    kinds = ["dense", "sparse05", "sparse01", "echelon", "lowrank", "deep", "dup", "zero", "identity", "ones"]
+    hosts, mats, ns = [], [], []
+    for i, (m, n) in enumerate(shapes * 2):
+        kind = kinds[i % len(kinds)]
+        A = make(kind, m, n, int(rng.integers(1 << 30))) if m and n else np.zeros((m, S.default_stride(n)),
+                                                                                  dtype=np.uint64)
+        hosts.append((A, m, n))
+        mats.append(dev(A))
+        ns.append(n)
+    for opts in (None, {"tile_words": 4}):
+        ds = [t.clone() for t in mats]
+        Ps, Qs, ranks = g.pls_batched(ds, ns, opts=opts)
+        torch.cuda.synchronize()
+        rk = ranks.cpu().numpy()
+        for i, (A, m, n) in enumerate(hosts):
+            R, P, Q, r = oracle.pls(A, m, n)
+            assert rk[i] == r, (i, m, n)
+            assert (Ps[i].cpu().numpy()[:m] == P[:m]).all(), i
+            assert (Qs[i].cpu().numpy()[:n] == Q[:n]).all(), i
+            if m and n:
+                W = S.words_per_row(n)
+                assert (host(ds[i])[:, :W] == R[:, :W]).all(), (i, m, n)
+
+
+def test_pls_batched_many_small_and_user_workspace(g):
+    """A batch of 300 small matrices of varied shape through a caller-owned
+    workspace, run twice (the workspace's previous contents do not matter)."""
+    rng = np.random.default_rng(8)
+    hosts, ns = [], []
+    for i in range(300):
+        m = int(rng.integers(1, 200))
+        n = int(rng.integers(1, 300))
+        p = [0.5, 0.1, 0.01][i % 3]
+        hosts.append((S.bernoulli(m, n, p, 5000 + i), m, n))
+        ns.append(n)
+    shapes = [(m, n, S.default_stride(n)) for (_, m, n) in hosts]
+    nbytes = g.pls_batched_workspace_bytes(shapes)
+    work = torch.empty(nbytes // 8 + 64, dtype=torch.int64, device="cuda")
+    want = [oracle.pls(A, m, n) for (A, m, n) in hosts]
+    for _ in range(2):
+        ds = [dev(A) for (A, _, _) in hosts]
+        Ps, Qs, ranks = g.pls_batched(ds, ns, work=work)
+        torch.cuda.synchronize()
+        rk = ranks.cpu().numpy()
+        for i, (A, m, n) in enumerate(hosts):
+            R, P, Q, r = want[i]
+            assert rk[i] == r
+            assert (Ps[i].cpu().numpy()[:m] == P[:m]).all()
+            assert (Qs[i].cpu().numpy()[:n] == Q[:n]).all()
+            assert (host(ds[i])[:, :S.words_per_row(n)] == R[:, :S.words_per_row(n)]).all()
