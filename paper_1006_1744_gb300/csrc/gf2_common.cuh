@@ -119,10 +119,11 @@ size_t align_up(size_t x, size_t a);
 
 // Workspace carve-up of the panel elimination for an m x n matrix.
 struct ElimLayout {
-    size_t state;   // PanelState
+    size_t state;   // PanelState[2]: panel b writes state b & 1 and reads the other
     size_t perm;    // int32[m]: position -> physical row
     size_t side;    // u64[2][m]: panel word of each physical row (double buffered)
     size_t pmask;   // u64[W]: pivot-column mask
+    size_t tlist;   // int32[m]: physical rows of the trailing positions of the current panel
     size_t out;     // u64[m * stride]: rows in final order (pls / rref), or the copy (rank)
     size_t rref_b;  // rref: non-pivot part of S, compacted
     size_t rref_x;  // rref: solved non-pivot part
@@ -132,10 +133,15 @@ struct ElimLayout {
 int64_t min_stride(int64_t n);
 ElimLayout elim_layout(int op, int64_t m, int64_t n);
 
+// The state a finished elimination leaves its rank in: the one of its last panel.
+__host__ __device__ inline PanelState *final_state(PanelState *st, int64_t W) { return st + ((W + 1) & 1); }
+
 struct Elim {
     uint64_t *A;      // matrix being eliminated (caller's A, or the copy for rank)
     int64_t m, n, stride, W;
-    PanelState *st;
+    PanelState *st;   // the two panel states
+    PanelState *stf;  // final_state(st, W): rank and pivots after elim_run
+    int *tlist;
     int *perm;
     u64 *side;
     u64 *pmask;

@@ -15,6 +15,9 @@
 // writes exactly the forward-substitution multipliers).
 #include <climits>
 
+#include <algorithm>
+#include <mutex>
+
 #include "gf2_common.cuh"
 
 namespace {
@@ -34,13 +37,13 @@ __global__ void k_init(const uint64_t *__restrict__ A, int64_t stride, int *__re
         if (side0)
             side0[i] = A[(int64_t)i * stride];
     }
-    if (i == 0 && st) {
-        st->r_cur = 0;
-        st->r_next = 0;
-        st->kbar = 0;
-        st->status = 0;
-        st->zero_tail = 0;
-        st->J = 0;
+    if (i < 2 && st) {  // both panel states
+        st[i].r_cur = 0;
+        st[i].r_next = 0;
+        st[i].kbar = 0;
+        st[i].status = 0;
+        st[i].zero_tail = 0;
+        st[i].J = 0;
     }
 }
 
@@ -119,6 +122,7 @@ __device__ bool pivot_fast(const u64 *__restrict__ side, const int *__restrict__
 {
     const int lane = threadIdx.x;
     u64 rows[NSLOT];
+    int wph[NSLOT];  // physical row at position lane + 32 k
 #pragma unroll
     for (int k = 0; k < NSLOT; ++k) {
         const int i = lane + 32 * k;
@@ -128,7 +132,7 @@ __device__ bool pivot_fast(const u64 *__restrict__ side, const int *__restrict__
             ph = perm[r + i];
             w = side[ph];
         }
-        S.Wph[i] = ph;
+        wph[k] = ph;
         rows[k] = w;
     }
     // column form: lane l <- columns l (c0) and l + 32 (c1) over positions 0..127
@@ -140,22 +144,20 @@ __device__ bool pivot_fast(const u64 *__restrict__ side, const int *__restrict__
     }
     u64 c0l = (u64)tc[0][0] | ((u64)tc[1][0] << 32), c0h = (u64)tc[2][0] | ((u64)tc[3][0] << 32);
     u64 c1l = (u64)tc[0][1] | ((u64)tc[1][1] << 32), c1h = (u64)tc[2][1] | ((u64)tc[3][1] << 32);
-    u64 G0 = 0, G1 = 0;  // Gauss-Jordan pivot rows at columns lane, lane + 32 (bit s = pivot s)
-    u64 X0 = 0, X1 = 0;  // columns lane, lane + 32 of U_J^-1 (bit s = row s)
-    u64 L0 = 0, L1 = 0;  // columns lane, lane + 32 of L^-1 (bit s = row s)
+    // pivot s: lane s & 31 keeps its position (at the time of the step) and column
+    int recp0 = 0, recp1 = 0, recj0 = 0, recj1 = 0;
     const bool all_rows = (m - r) <= WIN;
     int t = 0, j = 0;
     u64 J = 0, tb = 1;
+    // The loop is the bare elimination (find, swap, XOR); every by-product is
+    // recovered after it, so the loop-carried chain stays short.
     while (t < 64 && j < nbits && t < nwin) {
         const int jl = j & 31;
         const bool jh = j >= 32;
-        const u64 cl = jh ? c1l : c0l, ch = jh ? c1h : c0h;
-        const u64 cand = cl & ~(tb - 1ull);
-        const int pm = cand ? ctz64(cand) : (ch ? 64 + ctz64(ch) : 255);
-        const int p = __shfl_sync(GF2_FULL, pm, jl);
-        u64 cjl = __shfl_sync(GF2_FULL, cl, jl);
-        u64 cjh = __shfl_sync(GF2_FULL, ch, jl);
-        const u64 gj = __shfl_sync(GF2_FULL, jh ? G1 : G0, jl);
+        u64 cjl = __shfl_sync(GF2_FULL, jh ? c1l : c0l, jl);
+        u64 cjh = __shfl_sync(GF2_FULL, jh ? c1h : c0h, jl);
+        const u64 cand = cjl & ~(tb - 1ull);
+        const int p = cand ? ctz64(cand) : (cjh ? 64 + ctz64(cjh) : 255);
         if (p >= nwin) {
             if (!all_rows)
                 return false;  // a candidate may sit past the window
@@ -166,64 +168,89 @@ __device__ bool pivot_fast(const u64 *__restrict__ side, const int *__restrict__
             swap_rows128(c0l, c0h, t, p);
             swap_rows128(c1l, c1h, t, p);
             swap_rows128(cjl, cjh, t, p);
-            if (lane == 0) {
-                const int q = S.Wph[t];
-                S.Wph[t] = S.Wph[p];
-                S.Wph[p] = q;
+            const int kt = t >> 5, kp = p >> 5;
+            const int mine_t = kt ? wph[1] : wph[0];
+            const int mine_p = kp == 0 ? wph[0] : kp == 1 ? wph[1] : kp == 2 ? wph[2] : wph[3];
+            const int vt = __shfl_sync(GF2_FULL, mine_t, t & 31);
+            const int vp = __shfl_sync(GF2_FULL, mine_p, p & 31);
+#pragma unroll
+            for (int k = 0; k < NSLOT; ++k) {
+                wph[k] = (k == kt && lane == (t & 31)) ? vp : wph[k];
+                wph[k] = (k == kp && lane == (p & 31)) ? vt : wph[k];
             }
         }
-        if (lane == 0) {
-            S.sPpos[t] = r + p;
-            S.sPcol[t] = j;
+        if (t < 32) {
+            recp0 = lane == t ? p : recp0;
+            recj0 = lane == t ? j : recj0;
+        } else {
+            recp1 = lane == t - 32 ? p : recp1;
+            recj1 = lane == t - 32 ? j : recj1;
         }
         // rows below the pivot with a 1 in column j get the pivot row on columns > j
         const u64 rl = cjl & ~((tb << 1) - 1ull), rh = cjh;
-        const bool pb0 = (c0l & tb) != 0, pb1 = (c1l & tb) != 0;  // pivot row's bits at my columns
-        const u64 k0 = (lane > j && pb0) ? ~0ull : 0ull;
-        const u64 k1 = (lane + 32 > j && pb1) ? ~0ull : 0ull;
+        const u64 k0 = (lane > j && (c0l & tb)) ? ~0ull : 0ull;
+        const u64 k1 = (lane + 32 > j && (c1l & tb)) ? ~0ull : 0ull;
         c0l ^= rl & k0;
         c0h ^= rh & k0;
         c1l ^= rl & k1;
         c1h ^= rh & k1;
-        // Gauss-Jordan: pivot row t joins, column j is cleared from the earlier ones;
-        // column t of U_J^-1 is the set of earlier rows that were cleared, plus t
-        G0 |= pb0 ? tb : 0ull;
-        G1 |= pb1 ? tb : 0ull;
-        const u64 mu = gj & (tb - 1ull);
-        G0 ^= (G0 & tb) ? mu : 0ull;
-        G1 ^= (G1 & tb) ? mu : 0ull;
-        if (lane == (t & 31)) {
-            if (t < 32)
-                X0 = mu | tb;
-            else
-                X1 = mu | tb;
-        }
-        // multipliers of pivot row t (its bits at the earlier pivot columns) and row t of
-        // L^-1: L^-1[t] = e_t + sum of the L^-1[s] its multipliers select
-        const u64 rowbits = (u64)__ballot_sync(GF2_FULL, pb0) | ((u64)__ballot_sync(GF2_FULL, pb1) << 32);
-        const u64 left = rowbits & ((1ull << j) - 1ull);
-        const u64 xlt = (J == tb - 1ull) ? left : pext64(left, J);
-        if (lane == 0)
-            S.sXl[t] = xlt;
-        L0 |= (((u64)(__popcll(xlt & L0) & 1)) << t) | ((u64)(lane == t) << t);
-        L1 |= (((u64)(__popcll(xlt & L1) & 1)) << t) | ((u64)(lane + 32 == t) << t);
         J |= 1ull << j;
         ++j;
         ++t;
         tb <<= 1;
     }
-    // back to row form: pivot rows (positions < 64) and rows of U_J^-1
+#pragma unroll
+    for (int k = 0; k < NSLOT; ++k)
+        S.Wph[lane + 32 * k] = wph[k];
+    // pivot rows (positions < t) back in row form: the Gaussian-PLS panel word,
+    // multipliers of L at the earlier pivot columns, 1 at its own, reduced bits right
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
         const u64 rw = (u64)bt32((unsigned)(c0l >> (32 * k)), lane) |
                        ((u64)bt32((unsigned)(c1l >> (32 * k)), lane) << 32);
+        const int s2 = lane + 32 * k;
+        if (s2 < t) {
+            const int js = k ? recj1 : recj0;
+            S.sNew[s2] = rw;
+            S.sPpos[s2] = r + (k ? recp1 : recp0);
+            S.sPcol[s2] = js;
+            // multipliers over the earlier pivots, and the U_J row (pivot columns >= js)
+            S.sXl[s2] = pext64(rw & lowmask(js), J);
+            S.sVw[s2] = pext64(rw & ~lowmask(js), J);
+        }
+    }
+    __syncwarp();
+    // columns lane, lane + 32 of U_J^-1 (rows bottom-up: row s = e_s + the rows k > s
+    // that U_J's row s selects) and of L^-1 (rows top-down: row s = e_s + the rows
+    // k < s that the multipliers of pivot s select), as four independent chains in
+    // one loop; bit s of a column is the parity of (selector & column)
+    u64 X0 = 0, X1 = 0, L0 = 0, L1 = 0;
+    {
+        const u64 own0 = 1ull << lane, own1 = 1ull << (lane + 32);
+        u64 bu = t > 0 ? 1ull << (t - 1) : 0ull, bl = 1ull;
+        for (int i = 0; i < t; ++i) {
+            const u64 us = S.sVw[t - 1 - i], xl = S.sXl[i];
+            const u64 a0 = us & X0, a1 = us & X1, c0 = xl & L0, c1 = xl & L1;
+            const bool pa0 = __popc((unsigned)a0 ^ (unsigned)(a0 >> 32)) & 1;
+            const bool pa1 = __popc((unsigned)a1 ^ (unsigned)(a1 >> 32)) & 1;
+            const bool pc0 = __popc((unsigned)c0 ^ (unsigned)(c0 >> 32)) & 1;
+            const bool pc1 = __popc((unsigned)c1 ^ (unsigned)(c1 >> 32)) & 1;
+            X0 |= (pa0 ? bu : 0ull) ^ (own0 & bu);
+            X1 |= (pa1 ? bu : 0ull) ^ (own1 & bu);
+            L0 |= (pc0 ? bl : 0ull) ^ (own0 & bl);
+            L1 |= (pc1 ? bl : 0ull) ^ (own1 & bl);
+            bu >>= 1;
+            bl <<= 1;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
         const u64 ui = (u64)bt32((unsigned)(X0 >> (32 * k)), lane) |
                        ((u64)bt32((unsigned)(X1 >> (32 * k)), lane) << 32);
         const u64 li = (u64)bt32((unsigned)(L0 >> (32 * k)), lane) |
                        ((u64)bt32((unsigned)(L1 >> (32 * k)), lane) << 32);
         const int s2 = lane + 32 * k;
         if (s2 < t) {
-            S.sNew[s2] = rw;
             S.sUi[s2] = ui;
             S.sLi[s2] = li;
         }
@@ -539,16 +566,17 @@ __device__ void pivot_rows(const u64 *__restrict__ side, int *__restrict__ perm,
     J_out = J;
 }
 
-__device__ __forceinline__ void pivot_panel(const u64 *__restrict__ side, int *__restrict__ perm, PanelState *st,
-                                            int64_t *P, int64_t *Q, int m, int b, int nbits)
+__device__ __forceinline__ void pivot_panel(const u64 *__restrict__ side, int *__restrict__ perm,
+                                            const PanelState *__restrict__ st_prev, PanelState *st, int64_t *P,
+                                            int64_t *Q, int m, int b, int nbits)
 {
     __shared__ PivotShared S;
     __shared__ u64 sXp[64], sXm[64];
     const int lane = threadIdx.x;
-    const int r = st->r_next;
+    const int r = st_prev->r_next;
     int t = 0;
     u64 J = 0;
-    const int nwin = (r < m && !st->zero_tail) ? min(WIN, m - r) : 0;
+    const int nwin = (r < m && !st_prev->zero_tail) ? min(WIN, m - r) : 0;
     if (nwin > 0) {
         const bool fast = pivot_fast(side, perm, r, m, nwin, nbits, t, J, S);
         __syncwarp();
@@ -588,15 +616,23 @@ __device__ __forceinline__ void pivot_panel(const u64 *__restrict__ side, int *_
     sXm[lane] = 0;
     sXm[lane + 32] = 0;
     __syncwarp();
-    for (int s2 = lane; s2 < t; s2 += 32) {
-        u64 ui = S.sUi[s2], mrow = 0;
-        while (ui) {
-            const int k = ctz64(ui);
-            ui &= ui - 1;
-            mrow ^= S.sLi[k];
+    {
+        // rows lane, lane + 32 of M = U_J^-1 L^-1 (uniform loop: every lane reads the same L^-1 row)
+        const u64 ua = lane < t ? S.sUi[lane] : 0ull, ub = lane + 32 < t ? S.sUi[lane + 32] : 0ull;
+        u64 ma = 0, mb = 0;
+        for (int k = 0; k < t; ++k) {
+            const u64 lk = S.sLi[k];
+            ma ^= ((ua >> k) & 1ull) ? lk : 0ull;
+            mb ^= ((ub >> k) & 1ull) ? lk : 0ull;
         }
-        sXp[S.sPcol[s2]] = mrow;
-        sXm[S.sPcol[s2]] = pdep64(S.sUi[s2], J);
+        if (lane < t) {
+            sXp[S.sPcol[lane]] = ma;
+            sXm[S.sPcol[lane]] = pdep64(ua, J);
+        }
+        if (lane + 32 < t) {
+            sXp[S.sPcol[lane + 32]] = mb;
+            sXm[S.sPcol[lane + 32]] = pdep64(ub, J);
+        }
     }
     __syncwarp();
     for (int c = lane; c < 64; c += 32) {
@@ -618,10 +654,10 @@ __device__ __forceinline__ void pivot_panel(const u64 *__restrict__ side, int *_
 }
 
 __global__ void __launch_bounds__(32, 1)
-k_pivot(const u64 *__restrict__ side, int *__restrict__ perm, PanelState *st, int64_t *P, int64_t *Q, int m,
-        int b, int nbits)
+k_pivot(const u64 *__restrict__ side, int *__restrict__ perm, const PanelState *__restrict__ st_prev, PanelState *st,
+        int64_t *P, int64_t *Q, int m, int b, int nbits)
 {
-    pivot_panel(side, perm, st, P, Q, m, b, nbits);
+    pivot_panel(side, perm, st_prev, st, P, Q, m, b, nbits);
 }
 
 // ---------------------------------------------------------------------------
@@ -642,14 +678,19 @@ k_pivot(const u64 *__restrict__ side, int *__restrict__ perm, PanelState *st, in
 // keeps its tables while consecutive work items share a tile, and keeps RPT
 // rows per thread in flight.
 // ---------------------------------------------------------------------------
-template <int TW, int RPT>
+// REST = the look-ahead split: word b + 1 (the next panel's word) and the
+// next side buffer are left to next_panel, and the trailing rows come from the
+// list next_panel wrote (the row order may be changing under a concurrent
+// pivot search of panel b + 1).
+template <int TW, int RPT, int NT, bool REST>
 __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_cur,
                                             u64 *__restrict__ side_nxt, const int *__restrict__ perm,
-                                            const PanelState *__restrict__ st, uint64_t *__restrict__ out,
-                                            int64_t ostride, int m, int W, int b, int cta, int ncta)
+                                            const int *__restrict__ tlist, const PanelState *__restrict__ st,
+                                            uint64_t *__restrict__ out, int64_t ostride, int m, int W, int b, int cta,
+                                            int ncta)
 {
     constexpr int TPR = TW / 2;     // threads per row, two words each
-    constexpr int RPP = 256 / TPR;  // rows per thread slot and pass
+    constexpr int RPP = NT / TPR;   // rows per thread slot and pass
     constexpr int BPL = 8 / TPR;    // z-table bytes per thread
     extern __shared__ __align__(16) u64 sm[];
     u64 *sT = sm;                 // [8][256][TW]  Gray-code tables of the pivot rows O
@@ -664,8 +705,10 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
         return;
     const int tid = threadIdx.x;
     if (kbar == 0) {
+        if (REST)
+            return;
         if (b + 1 < W)
-            for (int p = r + cta * 256 + tid; p < m; p += ncta * 256) {
+            for (int p = r + cta * NT + tid; p < m; p += ncta * NT) {
                 int ph = perm[p];
                 side_nxt[ph] = A[(int64_t)ph * stride + b + 1];
             }
@@ -688,7 +731,7 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
     else if (tid < 128)
         sMap[tid] = st->xmap[tid - 64];
     __syncthreads();
-    for (int e = tid; e < 8 * 256; e += 256) {
+    for (int e = tid; e < 8 * 256; e += NT) {
         const int q = e >> 8, v = e & 255;
         u64 zz = 0, xx = 0;
 #pragma unroll
@@ -710,7 +753,7 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
         const int wbase = wstart + tile * TW;
         if (tile != cur_tile) {
             __syncthreads();
-            for (int e = tid; e < 64 * TW; e += 256) {
+            for (int e = tid; e < 64 * TW; e += NT) {
                 const int s2 = e / TW, wi = e % TW;
                 u64 v = 0;
                 if (s2 < kbar && wbase + wi < W)
@@ -718,7 +761,7 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
                 sO[e] = v;
             }
             __syncthreads();
-            for (int e = tid; e < ng * TW * 16; e += 256) {
+            for (int e = tid; e < ng * TW * 16; e += NT) {
                 const int vh = e & 15, gw = e >> 4, wi = gw % TW, g = gw / TW;
                 const u64 *Og = sO + (8 * g) * TW + wi;
                 u64 cur = 0;
@@ -752,7 +795,7 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
                 const int p = pb + j * RPP + rg;
                 valid[j] = p < p_end;
                 isp[j] = valid[j] && p < r + kbar;
-                ph[j] = !valid[j] ? 0 : (isp[j] ? st->prow[p - r] : perm[p]);
+                ph[j] = !valid[j] ? 0 : (isp[j] ? st->prow[p - r] : (REST ? tlist[p - r - kbar] : perm[p]));
             }
             // (b) their panel words and current words of the tile, all in flight
 #pragma unroll
@@ -777,19 +820,28 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
             for (int j = 0; j < RPT; ++j) {
                 const int p = pb + j * RPP + rg;
                 u64 zz = 0;
+                {
+                    // this thread's BPL bytes of the panel word
+                    const unsigned mine = (unsigned)(wv[j] >> (8 * BPL * sub));
 #pragma unroll
-                for (int q = sub * BPL; q < (sub + 1) * BPL; ++q)
-                    zz ^= sZ[(q << 8) | (int)((wv[j] >> (8 * q)) & 255ull)];
+                    for (int q = 0; q < BPL; ++q)
+                        zz ^= sZ[((sub * BPL + q) << 8) | (int)((mine >> (8 * q)) & 255u)];
+                }
 #pragma unroll
                 for (int o = 1; o < TPR; o <<= 1)
                     zz ^= __shfl_xor_sync(gmask, zz, o);
                 const u64 z = isp[j] ? st->zpiv[p - r] : zz;
+                const unsigned zw[2] = {(unsigned)z, (unsigned)(z >> 32)};
                 u64 acc0 = 0, acc1 = 0;
-                for (int g = 0; g < ng; ++g) {
-                    const int v = (int)((z >> (8 * g)) & 255ull);
-                    const ulonglong2 e2 = *reinterpret_cast<const ulonglong2 *>(sT + (g * 256 + v) * TW + 2 * sub);
-                    acc0 ^= e2.x;
-                    acc1 ^= e2.y;
+                const u64 *tb0 = sT + 2 * sub;
+#pragma unroll
+                for (int g = 0; g < 8; ++g) {
+                    if (g < ng) {
+                        const int v = (int)((zw[g >> 2] >> (8 * (g & 3))) & 255u);
+                        const ulonglong2 e2 = *reinterpret_cast<const ulonglong2 *>(tb0 + (g * 256 + v) * TW);
+                        acc0 ^= e2.x;
+                        acc1 ^= e2.y;
+                    }
                 }
                 if (!valid[j] || !wact)
                     continue;
@@ -797,9 +849,9 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
                     // pivot row t = p - r: final row U_t, written in final position
                     if (out) {
                         uint64_t *o = out + (int64_t)p * ostride;
-                        if (w0 >= b)
+                        if (w0 >= b && !(REST && w0 == b + 1))
                             o[w0] = (w0 == b) ? st->newblk[p - r] : acc0;
-                        if (two)
+                        if (two && !(REST && w0 + 1 == b + 1))
                             o[w0 + 1] = (w0 + 1 == b) ? st->newblk[p - r] : acc1;
                     }
                     continue;
@@ -821,7 +873,12 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
                     n1 ^= acc1;
                 }
                 uint64_t *a = A + (int64_t)ph[j] * stride + w0;
-                if (two) {
+                if (REST && w0 == b + 1) {
+                    if (two)
+                        a[1] = n1;  // word b + 1 belongs to next_panel
+                } else if (REST && w0 + 1 == b + 1) {
+                    a[0] = n0;
+                } else if (two) {
                     ulonglong2 v2;
                     v2.x = n0;
                     v2.y = n1;
@@ -829,7 +886,7 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
                 } else {
                     a[0] = n0;
                 }
-                if (b + 1 < W) {
+                if (!REST && b + 1 < W) {
                     if (w0 == b + 1)
                         side_nxt[ph[j]] = n0;
                     else if (two && w0 + 1 == b + 1)
@@ -840,13 +897,109 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
     }
 }
 
-template <int TW, int RPT, int MINB>
-__global__ void __launch_bounds__(256, MINB)
+template <int TW, int RPT, int NT, int MINB, bool REST>
+__global__ void __launch_bounds__(NT, MINB)
 k_sweep(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_cur, u64 *__restrict__ side_nxt,
-        const int *__restrict__ perm, const PanelState *__restrict__ st, uint64_t *__restrict__ out,
-        int64_t ostride, int m, int W, int b)
+        const int *__restrict__ perm, const int *__restrict__ tlist, const PanelState *__restrict__ st,
+        uint64_t *__restrict__ out, int64_t ostride, int m, int W, int b)
 {
-    sweep_panel<TW, RPT>(A, stride, side_cur, side_nxt, perm, st, out, ostride, m, W, b, blockIdx.x, gridDim.x);
+    sweep_panel<TW, RPT, NT, REST>(A, stride, side_cur, side_nxt, perm, tlist, st, out, ostride, m, W, b, blockIdx.x,
+                               gridDim.x);
+}
+
+// ---------------------------------------------------------------------------
+// Look-ahead part of the sweep of panel b: word b + 1 only -- the word the
+// pivot search of panel b + 1 reads -- for every trailing row (also stored in
+// the next side buffer) and for the pivot rows (to `out`), with one Gray-code
+// table set over that single word. It also records the physical rows of the
+// trailing positions, so that the rest of the sweep never reads the row order
+// while the next pivot search changes it. One trailing row per thread.
+// ---------------------------------------------------------------------------
+constexpr int NEXT_THREADS = 256;
+
+__global__ void __launch_bounds__(NEXT_THREADS)
+k_next(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_cur, u64 *__restrict__ side_nxt,
+       const int *__restrict__ perm, int *__restrict__ tlist, const PanelState *__restrict__ st,
+       uint64_t *__restrict__ out, int64_t ostride, int m, int W, int b)
+{
+    __shared__ u64 sT1[8 * 256];  // sums of the pivot rows' word b + 1, one table per 8 pivots
+    __shared__ u64 sZ1[8 * 256];  // raw panel byte -> coordinates over the pivot rows
+    __shared__ u64 sO1[64];
+    __shared__ u64 sMap1[64];
+    const int r = st->r_cur, kbar = st->kbar;
+    const int p0 = r + kbar;  // first trailing position
+    const int tid = threadIdx.x;
+    const int g0 = blockIdx.x * NEXT_THREADS + tid, gs = gridDim.x * NEXT_THREADS;
+    const bool has_next = b + 1 < W;
+    if (kbar == 0) {
+        for (int p = p0 + g0; p < m; p += gs) {
+            const int ph = perm[p];
+            tlist[p - p0] = ph;
+            if (has_next)
+                side_nxt[ph] = A[(int64_t)ph * stride + b + 1];
+        }
+        return;
+    }
+    if (tid < 64) {
+        sMap1[tid] = st->zmap[tid];
+        sO1[tid] = (has_next && tid < kbar) ? A[(int64_t)st->prow[tid] * stride + b + 1] : 0ull;
+    }
+    __syncthreads();
+    for (int e = tid; e < 8 * 256; e += NEXT_THREADS) {
+        const int q = e >> 8, v = e & 255;
+        u64 zz = 0;
+#pragma unroll
+        for (int bit = 0; bit < 8; ++bit)
+            if ((v >> bit) & 1)
+                zz ^= sMap1[8 * q + bit];
+        sZ1[e] = zz;
+    }
+    const int ng = (kbar + 7) >> 3;
+    // Gray-code enumeration: T[hi << 4 | gray(i)] from T[hi << 4 | gray(i - 1)] by one row
+    for (int e = tid; e < ng * 16; e += NEXT_THREADS) {
+        const int vh = e & 15, g = e >> 4;
+        const u64 *Og = sO1 + 8 * g;
+        u64 cur = 0;
+#pragma unroll
+        for (int bit = 0; bit < 4; ++bit)
+            if ((vh >> bit) & 1)
+                cur ^= Og[4 + bit];
+        u64 *Tg = sT1 + g * 256 + (vh << 4);
+        Tg[0] = cur;
+#pragma unroll
+        for (int i = 1; i < 16; ++i) {
+            cur ^= Og[__ffs(i) - 1];
+            Tg[i ^ (i >> 1)] = cur;
+        }
+    }
+    __syncthreads();
+    for (int p = p0 + g0; p < m; p += gs) {
+        const int ph = perm[p];
+        tlist[p - p0] = ph;
+        if (!has_next)
+            continue;
+        const u64 wv = side_cur[ph];
+        uint64_t *a = A + (int64_t)ph * stride + b + 1;
+        const u64 old = *a;
+        u64 z = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            z ^= sZ1[(q << 8) | (int)((wv >> (8 * q)) & 255ull)];
+        u64 acc = 0;
+        for (int g = 0; g < ng; ++g)
+            acc ^= sT1[g * 256 + (int)((z >> (8 * g)) & 255ull)];
+        const u64 nw = old ^ acc;
+        *a = nw;
+        side_nxt[ph] = nw;
+    }
+    if (has_next && out)
+        for (int s2 = g0; s2 < kbar; s2 += gs) {
+            const u64 z = st->zpiv[s2];
+            u64 acc = 0;
+            for (int g = 0; g < ng; ++g)
+                acc ^= sT1[g * 256 + (int)((z >> (8 * g)) & 255ull)];
+            out[(int64_t)(r + s2) * ostride + b + 1] = acc;
+        }
 }
 
 // ---------------------------------------------------------------------------
@@ -991,13 +1144,13 @@ constexpr size_t sweep_smem()
     return (size_t)(8 * 256 * TW + 2 * 8 * 256 + 64 * TW + 128) * sizeof(u64);
 }
 
-template <int TW, int RPT, int MINB>
-int launch_sweep(const gf2::Elim &e, int b)
+template <int TW, int RPT, int NT, int MINB, bool REST>
+int launch_sweep(const gf2::Elim &e, int b, cudaStream_t s)
 {
     static bool attr_set = false;  // per process; the attribute is per function
     constexpr size_t smem = sweep_smem<TW>();
     if (!attr_set) {
-        cudaError_t err = cudaFuncSetAttribute(k_sweep<TW, RPT, MINB>,
+        cudaError_t err = cudaFuncSetAttribute(k_sweep<TW, RPT, NT, MINB, REST>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess)
             return gf2::note_cuda(err);
@@ -1005,10 +1158,11 @@ int launch_sweep(const gf2::Elim &e, int b)
     }
     const u64 *cur = e.side + (size_t)(b & 1) * e.m;
     u64 *nxt = e.side + (size_t)((b + 1) & 1) * e.m;
-    const int tok = gf2::prof_begin(e.s);
-    k_sweep<TW, RPT, MINB><<<e.grid * MINB, 256, smem, e.s>>>(e.A, e.stride, cur, nxt, e.perm, e.st, e.out,
-                                                              e.ostride, (int)e.m, (int)e.W, b);
-    gf2::prof_end(e.s, GF2_PROF_SWEEP, tok);
+    const int tok = gf2::prof_begin(s);
+    k_sweep<TW, RPT, NT, MINB, REST><<<e.grid * MINB, NT, smem, s>>>(e.A, e.stride, cur, nxt, e.perm, e.tlist,
+                                                                   e.st + (b & 1), e.out, e.ostride, (int)e.m,
+                                                                   (int)e.W, b);
+    gf2::prof_end(s, GF2_PROF_SWEEP, tok);
     gf2::prof_launched(1);
     return gf2::note_cuda(cudaGetLastError());
 }
@@ -1027,13 +1181,13 @@ __global__ void k_init_b(const gf2::ElimDesc *__restrict__ D)
     }
     for (int w = g; w < d.W + 1; w += nt)
         d.pmask[w] = 0;
-    if (g == 0) {
-        d.st->r_cur = 0;
-        d.st->r_next = 0;
-        d.st->kbar = 0;
-        d.st->status = 0;
-        d.st->zero_tail = 0;
-        d.st->J = 0;
+    if (g < 2) {
+        d.st[g].r_cur = 0;
+        d.st[g].r_next = 0;
+        d.st[g].kbar = 0;
+        d.st[g].status = 0;
+        d.st[g].zero_tail = 0;
+        d.st[g].J = 0;
     }
 }
 
@@ -1041,7 +1195,7 @@ __global__ void __launch_bounds__(32, 1) k_pivot_b(const gf2::ElimDesc *__restri
 {
     const gf2::ElimDesc &d = D[idx[blockIdx.x]];
     const int nbits = min(64, d.n - 64 * b);
-    pivot_panel(d.side + (size_t)(b & 1) * d.m, d.perm, d.st, d.P, d.Q, d.m, b, nbits);
+    pivot_panel(d.side + (size_t)(b & 1) * d.m, d.perm, d.st + ((b + 1) & 1), d.st + (b & 1), d.P, d.Q, d.m, b, nbits);
 }
 
 template <int TW, int RPT, int MINB>
@@ -1058,21 +1212,22 @@ k_sweep_b(const gf2::ElimDesc *__restrict__ D, const int *__restrict__ idx, cons
             hi = mid - 1;
     }
     const gf2::ElimDesc &d = D[idx[lo]];
-    sweep_panel<TW, RPT>(d.A, d.stride, d.side + (size_t)(b & 1) * d.m, d.side + (size_t)((b + 1) & 1) * d.m, d.perm,
-                         d.st, d.out, d.ostride, d.m, d.W, b, (int)blockIdx.x - pre[lo], pre[lo + 1] - pre[lo]);
+    sweep_panel<TW, RPT, 256, false>(d.A, d.stride, d.side + (size_t)(b & 1) * d.m, d.side + (size_t)((b + 1) & 1) * d.m,
+                                d.perm, nullptr, d.st + (b & 1), d.out, d.ostride, d.m, d.W, b,
+                                (int)blockIdx.x - pre[lo], pre[lo + 1] - pre[lo]);
 }
 
 __global__ void k_gather_b(const gf2::ElimDesc *__restrict__ D)
 {
     const gf2::ElimDesc &d = D[blockIdx.y];
-    gather_rows(d.A, d.stride, d.perm, d.st, d.P, d.Q, d.out, d.ostride, d.m, d.n, d.W, d.rank, blockIdx.x,
-                gridDim.x);
+    gather_rows(d.A, d.stride, d.perm, gf2::final_state(d.st, d.W), d.P, d.Q, d.out, d.ostride, d.m, d.n, d.W, d.rank,
+                blockIdx.x, gridDim.x);
 }
 
 __global__ void k_pmask_b(const gf2::ElimDesc *__restrict__ D)
 {
     const gf2::ElimDesc &d = D[blockIdx.y];
-    pivot_mask(d.Q, d.st, d.pmask, blockIdx.x, gridDim.x);
+    pivot_mask(d.Q, gf2::final_state(d.st, d.W), d.pmask, blockIdx.x, gridDim.x);
 }
 
 __global__ void k_compress_b(const gf2::ElimDesc *__restrict__ D)
@@ -1080,7 +1235,7 @@ __global__ void k_compress_b(const gf2::ElimDesc *__restrict__ D)
     const gf2::ElimDesc &d = D[blockIdx.y];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < d.m)
-        compress_row(d.out, d.ostride, d.Q, d.pmask, d.st, d.m, i);
+        compress_row(d.out, d.ostride, d.Q, d.pmask, gf2::final_state(d.st, d.W), d.m, i);
 }
 
 // out -> A, one warp per row
@@ -1183,33 +1338,101 @@ int identity_fill(int64_t *P, int64_t m, int64_t *Q, int64_t n, int64_t *rank, c
     return note_cuda(cudaGetLastError());
 }
 
+// Side streams for the look-ahead (a few per device, created on first use) and
+// the events that order the two streams of one elimination.
+struct SideStreams {
+    std::mutex mu;
+    cudaStream_t s[64][4] = {};
+    unsigned next[64] = {};
+};
+static SideStreams g_side;
+
+static int side_stream(cudaStream_t *out)
+{
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess)
+        return note_cuda(err);
+    if (dev < 0 || dev >= 64)
+        return GF2_EINVAL;
+    std::lock_guard<std::mutex> lock(g_side.mu);
+    const unsigned k = g_side.next[dev]++ & 3u;
+    if (!g_side.s[dev][k] && (err = cudaStreamCreateWithFlags(&g_side.s[dev][k], cudaStreamNonBlocking)) != cudaSuccess)
+        return note_cuda(err);
+    *out = g_side.s[dev][k];
+    return GF2_OK;
+}
+
+struct EventSet {
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    ~EventSet()
+    {
+        for (cudaEvent_t x : ev)
+            if (x)
+                cudaEventDestroy(x);  // released once the recorded work completes
+    }
+    int create()
+    {
+        for (cudaEvent_t &x : ev) {
+            cudaError_t err = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+            if (err != cudaSuccess)
+                return note_cuda(err);
+        }
+        return GF2_OK;
+    }
+};
+
+// Panel elimination with a look-ahead of one panel. Panel b: the pivot search
+// (stream s), then the sweep's word b + 1 and trailing-row list (k_next, s),
+// then the rest of the sweep on the side stream t, which runs while the pivot
+// search of panel b + 1 proceeds on s. k_next of panel b + 1 waits for the rest
+// of panel b (both write words >= b + 2 of the same rows). Panel states and
+// side buffers alternate with the parity of b.
 int elim_run(const Elim &e)
 {
     const int m = (int)e.m;
     k_init<<<(m + 255) / 256, 256, 0, e.s>>>(e.A, e.stride, e.perm, e.side, e.st, m);
     prof_launched(1);
     int rc = note_cuda(cudaGetLastError());
-    if (rc)
+    if (rc || e.W == 0)
         return rc;
+    cudaStream_t t = nullptr;
+    EventSet E;
+    if ((rc = side_stream(&t)) || (rc = E.create()))
+        return rc;
+    cudaEvent_t ev_fork = E.ev[0], ev_next = E.ev[1], ev_rest = E.ev[2];
+    if ((rc = note_cuda(cudaEventRecord(ev_fork, e.s))) || (rc = note_cuda(cudaStreamWaitEvent(t, ev_fork, 0))))
+        return rc;
+    const int next_ctas = std::max(1, std::min((m + NEXT_THREADS - 1) / NEXT_THREADS, 2 * sm_count()));
     for (int b = 0; b < (int)e.W; ++b) {
         const int nbits = (int)((e.n - 64ll * b) < 64 ? (e.n - 64ll * b) : 64);
-        const int tok = prof_begin(e.s);
-        k_pivot<<<1, 32, 0, e.s>>>(e.side + (size_t)(b & 1) * e.m, e.perm, e.st, e.P, e.Q, m, b, nbits);
+        const u64 *cur = e.side + (size_t)(b & 1) * e.m;
+        u64 *nxt = e.side + (size_t)((b + 1) & 1) * e.m;
+        PanelState *stb = e.st + (b & 1);
+        int tok = prof_begin(e.s);
+        k_pivot<<<1, 32, 0, e.s>>>(cur, e.perm, e.st + ((b + 1) & 1), stb, e.P, e.Q, m, b, nbits);
         prof_end(e.s, GF2_PROF_PIVOT, tok);
         prof_launched(1);
-        rc = note_cuda(cudaGetLastError());
-        if (rc)
+        if ((rc = note_cuda(cudaGetLastError())))
             return rc;
-        rc = e.tile_words == 4 ? launch_sweep<4, 4, 2>(e, b) : launch_sweep<8, 4, 1>(e, b);
-        if (rc)
+        if (b > 0 && (rc = note_cuda(cudaStreamWaitEvent(e.s, ev_rest, 0))))
+            return rc;
+        k_next<<<next_ctas, NEXT_THREADS, 0, e.s>>>(e.A, e.stride, cur, nxt, e.perm, e.tlist, stb, e.out, e.ostride, m,
+                                                  (int)e.W, b);
+        prof_launched(1);
+        if ((rc = note_cuda(cudaGetLastError())) || (rc = note_cuda(cudaEventRecord(ev_next, e.s))) ||
+            (rc = note_cuda(cudaStreamWaitEvent(t, ev_next, 0))))
+            return rc;
+        rc = e.tile_words == 4 ? launch_sweep<4, 4, 256, 2, true>(e, b, t) : launch_sweep<8, 2, 512, 1, true>(e, b, t);
+        if (rc || (rc = note_cuda(cudaEventRecord(ev_rest, t))))
             return rc;
     }
-    return GF2_OK;
+    return note_cuda(cudaStreamWaitEvent(e.s, ev_rest, 0));
 }
 
 int elim_gather(const Elim &e, int64_t *rank)
 {
-    k_gather<<<2 * sm_count(), 256, 0, e.s>>>(e.A, e.stride, e.perm, e.st, e.P, e.Q, e.out, e.ostride,
+    k_gather<<<2 * sm_count(), 256, 0, e.s>>>(e.A, e.stride, e.perm, e.stf, e.P, e.Q, e.out, e.ostride,
                                               (int)e.m, (int)e.n, (int)e.W, rank);
     prof_launched(1);
     return note_cuda(cudaGetLastError());
@@ -1220,8 +1443,8 @@ int pls_finish(const Elim &e)
     cudaError_t err = cudaMemsetAsync(e.pmask, 0, (size_t)e.W * sizeof(u64), e.s);
     if (err != cudaSuccess)
         return note_cuda(err);
-    k_pmask<<<64, 256, 0, e.s>>>(e.Q, e.st, e.pmask);
-    k_compress<<<(int)((e.m + 127) / 128), 128, 0, e.s>>>(e.out, e.ostride, e.Q, e.pmask, e.st, (int)e.m);
+    k_pmask<<<64, 256, 0, e.s>>>(e.Q, e.stf, e.pmask);
+    k_compress<<<(int)((e.m + 127) / 128), 128, 0, e.s>>>(e.out, e.ostride, e.Q, e.pmask, e.stf, (int)e.m);
     prof_launched(2);
     int rc = note_cuda(cudaGetLastError());
     if (rc)

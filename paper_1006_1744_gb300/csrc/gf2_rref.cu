@@ -274,11 +274,11 @@ int rref_finish(const Elim &e, const ElimLayout &L, char *work, int64_t *rank, i
     cudaError_t err = cudaMemsetAsync(e.pmask, 0, (size_t)W * sizeof(u64), e.s);
     if (err != cudaSuccess)
         return note_cuda(err);
-    k_pmask2<<<64, 256, 0, e.s>>>(e.Q, e.st, e.pmask);
+    k_pmask2<<<64, 256, 0, e.s>>>(e.Q, e.stf, e.pmask);
     const int rmax = m < n ? m : n;
-    k_rref_compact<<<(rmax + 127) / 128, 128, 0, e.s>>>(e.out, e.ostride, e.Q, e.pmask, e.st, e.A, Bc, sb, n, W);
+    k_rref_compact<<<(rmax + 127) / 128, 128, 0, e.s>>>(e.out, e.ostride, e.Q, e.pmask, e.stf, e.A, Bc, sb, n, W);
     const int nblk = (rmax + 63) / 64;
-    k_diag_inv<<<(nblk + 3) / 4, 128, 0, e.s>>>(e.A, e.stride, e.st, Dinv, nblk);
+    k_diag_inv<<<(nblk + 3) / 4, 128, 0, e.s>>>(e.A, e.stride, e.stf, Dinv, nblk);
     prof_launched(3);
     int rc = note_cuda(cudaGetLastError());
     if (rc)
@@ -294,15 +294,15 @@ int rref_finish(const Elim &e, const ElimLayout &L, char *work, int64_t *rank, i
     }
     for (int q = nblk - 1; q >= 0; --q) {
         const int tok = prof_begin(e.s);
-        k_rref_step<<<grid, 256, smem, e.s>>>(Bc, Xc, sb, e.A, e.stride, Dinv, e.st, n, q);
+        k_rref_step<<<grid, 256, smem, e.s>>>(Bc, Xc, sb, e.A, e.stride, Dinv, e.stf, n, q);
         prof_end(e.s, GF2_PROF_RREF, tok);
         prof_launched(1);
         rc = note_cuda(cudaGetLastError());
         if (rc)
             return rc;
     }
-    k_rref_scatter<<<(m + 127) / 128, 128, 0, e.s>>>(e.A, e.stride, Xc, sb, e.Q, e.pmask, e.st, m, n, W);
-    k_rref_outputs<<<32, 256, 0, e.s>>>(e.Q, e.st, n, pivots, rank);
+    k_rref_scatter<<<(m + 127) / 128, 128, 0, e.s>>>(e.A, e.stride, Xc, sb, e.Q, e.pmask, e.stf, m, n, W);
+    k_rref_outputs<<<32, 256, 0, e.s>>>(e.Q, e.stf, n, pivots, rank);
     prof_launched(2);
     return note_cuda(cudaGetLastError());
 }
