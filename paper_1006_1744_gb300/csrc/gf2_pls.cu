@@ -121,95 +121,82 @@ __device__ bool pivot_fast(const u64 *__restrict__ side, const int *__restrict__
                            int nbits, int &t_out, u64 &J_out, PivotShared &S)
 {
     const int lane = threadIdx.x;
-    u64 rows[NSLOT];
-    int wph[NSLOT];  // physical row at position lane + 32 k
+    // lane l holds the window rows at initial positions l + 32 k; a swap of positions
+    // only relabels two rows, no row moves
+    u64 row[NSLOT];
+    int pos[NSLOT], phys[NSLOT];
+    bool act[NSLOT];
 #pragma unroll
     for (int k = 0; k < NSLOT; ++k) {
         const int i = lane + 32 * k;
-        int ph = 0;
-        u64 w = 0;
-        if (i < nwin) {
-            ph = perm[r + i];
-            w = side[ph];
-        }
-        wph[k] = ph;
-        rows[k] = w;
+        act[k] = i < nwin;
+        phys[k] = act[k] ? perm[r + i] : 0;
+        pos[k] = i;
     }
-    // column form: lane l <- columns l (c0) and l + 32 (c1) over positions 0..127
-    unsigned tc[NSLOT][2];
 #pragma unroll
-    for (int k = 0; k < NSLOT; ++k) {
-        tc[k][0] = bt32((unsigned)rows[k], lane);
-        tc[k][1] = bt32((unsigned)(rows[k] >> 32), lane);
-    }
-    u64 c0l = (u64)tc[0][0] | ((u64)tc[1][0] << 32), c0h = (u64)tc[2][0] | ((u64)tc[3][0] << 32);
-    u64 c1l = (u64)tc[0][1] | ((u64)tc[1][1] << 32), c1h = (u64)tc[2][1] | ((u64)tc[3][1] << 32);
-    // pivot s: lane s & 31 keeps its position (at the time of the step) and column
+    for (int k = 0; k < NSLOT; ++k)
+        row[k] = act[k] ? side[phys[k]] : 0ull;
+    // pivot s: lane s & 31 keeps its panel word, position (at the time of the step) and column
+    u64 nw0 = 0, nw1 = 0;
     int recp0 = 0, recp1 = 0, recj0 = 0, recj1 = 0;
     const bool all_rows = (m - r) <= WIN;
     int t = 0, j = 0;
-    u64 J = 0, tb = 1;
-    // The loop is the bare elimination (find, swap, XOR); every by-product is
-    // recovered after it, so the loop-carried chain stays short.
+    u64 J = 0;
     while (t < 64 && j < nbits && t < nwin) {
-        const int jl = j & 31;
-        const bool jh = j >= 32;
-        u64 cjl = __shfl_sync(GF2_FULL, jh ? c1l : c0l, jl);
-        u64 cjh = __shfl_sync(GF2_FULL, jh ? c1h : c0h, jl);
-        const u64 cand = cjl & ~(tb - 1ull);
-        const int p = cand ? ctz64(cand) : (cjh ? 64 + ctz64(cjh) : 255);
-        if (p >= nwin) {
+        const int jw = j >> 5, jb = j & 31;
+        bool cand[NSLOT];
+        int key = INT_MAX;
+#pragma unroll
+        for (int k = 0; k < NSLOT; ++k) {
+            const unsigned h = jw ? (unsigned)(row[k] >> 32) : (unsigned)row[k];
+            cand[k] = act[k] && ((h >> jb) & 1u);
+            key = cand[k] ? min(key, (pos[k] << 7) | (k << 5) | lane) : key;
+        }
+        // first candidate in the current row order
+        const int best = __reduce_min_sync(GF2_FULL, key);
+        if (best == INT_MAX) {
             if (!all_rows)
                 return false;  // a candidate may sit past the window
             ++j;               // zero column among all remaining rows
             continue;
         }
-        if (p != t) {
-            swap_rows128(c0l, c0h, t, p);
-            swap_rows128(c1l, c1h, t, p);
-            swap_rows128(cjl, cjh, t, p);
-            const int kt = t >> 5, kp = p >> 5;
-            const int mine_t = kt ? wph[1] : wph[0];
-            const int mine_p = kp == 0 ? wph[0] : kp == 1 ? wph[1] : kp == 2 ? wph[2] : wph[3];
-            const int vt = __shfl_sync(GF2_FULL, mine_t, t & 31);
-            const int vp = __shfl_sync(GF2_FULL, mine_p, p & 31);
-#pragma unroll
-            for (int k = 0; k < NSLOT; ++k) {
-                wph[k] = (k == kt && lane == (t & 31)) ? vp : wph[k];
-                wph[k] = (k == kp && lane == (p & 31)) ? vt : wph[k];
-            }
-        }
+        const int p = best >> 7, slot = (best >> 5) & 3, plane = best & 31;
+        const u64 mine = slot == 0 ? row[0] : slot == 1 ? row[1] : slot == 2 ? row[2] : row[3];
+        const u64 prow = __shfl_sync(GF2_FULL, mine, plane);
         if (t < 32) {
+            nw0 = lane == t ? prow : nw0;
             recp0 = lane == t ? p : recp0;
             recj0 = lane == t ? j : recj0;
         } else {
+            nw1 = lane == t - 32 ? prow : nw1;
             recp1 = lane == t - 32 ? p : recp1;
             recj1 = lane == t - 32 ? j : recj1;
         }
-        // rows below the pivot with a 1 in column j get the pivot row on columns > j
-        const u64 rl = cjl & ~((tb << 1) - 1ull), rh = cjh;
-        const u64 k0 = (lane > j && (c0l & tb)) ? ~0ull : 0ull;
-        const u64 k1 = (lane + 32 > j && (c1l & tb)) ? ~0ull : 0ull;
-        c0l ^= rl & k0;
-        c0h ^= rh & k0;
-        c1l ^= rl & k1;
-        c1h ^= rh & k1;
+        // swap positions t and p: the pivot takes t (and leaves the candidates), the row
+        // at t takes p; rows below with a 1 in column j get the pivot row right of j
+        const u64 pm = prow & ~lowmask(j + 1);
+#pragma unroll
+        for (int k = 0; k < NSLOT; ++k) {
+            const bool isp = lane == plane && k == slot;
+            row[k] ^= (cand[k] && !isp) ? pm : 0ull;
+            pos[k] = isp ? t : (pos[k] == t ? p : pos[k]);
+            act[k] = act[k] && !isp;
+        }
         J |= 1ull << j;
         ++j;
         ++t;
-        tb <<= 1;
     }
 #pragma unroll
     for (int k = 0; k < NSLOT; ++k)
-        S.Wph[lane + 32 * k] = wph[k];
-    // pivot rows (positions < t) back in row form: the Gaussian-PLS panel word,
-    // multipliers of L at the earlier pivot columns, 1 at its own, reduced bits right
+        if (lane + 32 * k < nwin)
+            S.Wph[pos[k]] = phys[k];
+    // pivot rows: the Gaussian-PLS panel word -- multipliers of L at the earlier pivot
+    // columns, 1 at its own, reduced bits right of it
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-        const u64 rw = (u64)bt32((unsigned)(c0l >> (32 * k)), lane) |
-                       ((u64)bt32((unsigned)(c1l >> (32 * k)), lane) << 32);
         const int s2 = lane + 32 * k;
         if (s2 < t) {
+            const u64 rw = k ? nw1 : nw0;
             const int js = k ? recj1 : recj0;
             S.sNew[s2] = rw;
             S.sPpos[s2] = r + (k ? recp1 : recp0);
@@ -220,41 +207,6 @@ __device__ bool pivot_fast(const u64 *__restrict__ side, const int *__restrict__
         }
     }
     __syncwarp();
-    // columns lane, lane + 32 of U_J^-1 (rows bottom-up: row s = e_s + the rows k > s
-    // that U_J's row s selects) and of L^-1 (rows top-down: row s = e_s + the rows
-    // k < s that the multipliers of pivot s select), as four independent chains in
-    // one loop; bit s of a column is the parity of (selector & column)
-    u64 X0 = 0, X1 = 0, L0 = 0, L1 = 0;
-    {
-        const u64 own0 = 1ull << lane, own1 = 1ull << (lane + 32);
-        u64 bu = t > 0 ? 1ull << (t - 1) : 0ull, bl = 1ull;
-        for (int i = 0; i < t; ++i) {
-            const u64 us = S.sVw[t - 1 - i], xl = S.sXl[i];
-            const u64 a0 = us & X0, a1 = us & X1, c0 = xl & L0, c1 = xl & L1;
-            const bool pa0 = __popc((unsigned)a0 ^ (unsigned)(a0 >> 32)) & 1;
-            const bool pa1 = __popc((unsigned)a1 ^ (unsigned)(a1 >> 32)) & 1;
-            const bool pc0 = __popc((unsigned)c0 ^ (unsigned)(c0 >> 32)) & 1;
-            const bool pc1 = __popc((unsigned)c1 ^ (unsigned)(c1 >> 32)) & 1;
-            X0 |= (pa0 ? bu : 0ull) ^ (own0 & bu);
-            X1 |= (pa1 ? bu : 0ull) ^ (own1 & bu);
-            L0 |= (pc0 ? bl : 0ull) ^ (own0 & bl);
-            L1 |= (pc1 ? bl : 0ull) ^ (own1 & bl);
-            bu >>= 1;
-            bl <<= 1;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const u64 ui = (u64)bt32((unsigned)(X0 >> (32 * k)), lane) |
-                       ((u64)bt32((unsigned)(X1 >> (32 * k)), lane) << 32);
-        const u64 li = (u64)bt32((unsigned)(L0 >> (32 * k)), lane) |
-                       ((u64)bt32((unsigned)(L1 >> (32 * k)), lane) << 32);
-        const int s2 = lane + 32 * k;
-        if (s2 < t) {
-            S.sUi[s2] = ui;
-            S.sLi[s2] = li;
-        }
-    }
     t_out = t;
     J_out = J;
     return true;
@@ -566,86 +518,101 @@ __device__ void pivot_rows(const u64 *__restrict__ side, int *__restrict__ perm,
     J_out = J;
 }
 
+constexpr int PIVOT_THREADS = 128;  // warp 0 runs the elimination chain; all four share the rest
+
 __device__ __forceinline__ void pivot_panel(const u64 *__restrict__ side, int *__restrict__ perm,
                                             const PanelState *__restrict__ st_prev, PanelState *st, int64_t *P,
                                             int64_t *Q, int m, int b, int nbits)
 {
     __shared__ PivotShared S;
     __shared__ u64 sXp[64], sXm[64];
-    const int lane = threadIdx.x;
+    __shared__ u64 sJ;
+    __shared__ int sT, sFast;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = st_prev->r_next;
-    int t = 0;
-    u64 J = 0;
     const int nwin = (r < m && !st_prev->zero_tail) ? min(WIN, m - r) : 0;
-    if (nwin > 0) {
-        const bool fast = pivot_fast(side, perm, r, m, nwin, nbits, t, J, S);
-        __syncwarp();
-        if (!fast) {
-            pivot_rows(side, perm, r, m, nwin, nbits, t, J, S);
+    if (warp == 0) {
+        int t = 0, fast = 1;
+        u64 J = 0;
+        if (nwin > 0) {
+            fast = pivot_fast(side, perm, r, m, nwin, nbits, t, J, S) ? 1 : 0;
             __syncwarp();
-            // columns k = lane, lane + 32 of L^-1 from the multipliers, row by row
-            u64 L0 = 0, L1 = 0;
-            for (int s2 = 0; s2 < t; ++s2) {
-                const u64 xl = S.sXl[s2], tb = 1ull << s2;
-                L0 |= (((u64)(__popcll(xl & L0) & 1)) << s2) | (lane == s2 ? tb : 0ull);
-                L1 |= (((u64)(__popcll(xl & L1) & 1)) << s2) | (lane + 32 == s2 ? tb : 0ull);
+            if (!fast)
+                pivot_rows(side, perm, r, m, nwin, nbits, t, J, S);
+        }
+        if (lane == 0) {
+            sT = t;
+            sJ = J;
+            sFast = fast;
+        }
+    } else if (tid < 96) {
+        sXp[tid - 32] = 0;
+        sXm[tid - 32] = 0;
+    }
+    __syncthreads();
+    const int t = sT;
+    const u64 J = sJ;
+    // Inverses, one column per lane: warps 2, 3 -> L^-1 (rows top-down: row s = e_s +
+    // the rows k < s that pivot s's multipliers select); warps 0, 1 -> U_J^-1 (rows
+    // bottom-up: row s = e_s + the rows k > s that U_J's row s selects; the row-form
+    // path has it already). Bit s of a column = parity of (selector & column).
+    {
+        const bool isU = warp < 2;
+        if (!isU || sFast) {
+            const int col = lane + 32 * (warp & 1);
+            const u64 own = 1ull << col;
+            u64 X = 0, bit = isU ? (t > 0 ? 1ull << (t - 1) : 0ull) : 1ull;
+            for (int i = 0; i < t; ++i) {
+                const u64 a = (isU ? S.sVw[t - 1 - i] : S.sXl[i]) & X;
+                const bool par = __popc((unsigned)a ^ (unsigned)(a >> 32)) & 1;
+                X |= (par ? bit : 0ull) ^ (own & bit);
+                bit = isU ? bit >> 1 : bit << 1;
             }
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const u64 li = (u64)bt32((unsigned)(L0 >> (32 * k)), lane) |
-                               ((u64)bt32((unsigned)(L1 >> (32 * k)), lane) << 32);
-                if (lane + 32 * k < t)
-                    S.sLi[lane + 32 * k] = li;
-            }
+            // 32 columns x 64 rows -> the warp's 32-bit half of every row
+            unsigned *dst = reinterpret_cast<unsigned *>(isU ? S.sUi : S.sLi);
+            const unsigned lo = bt32((unsigned)X, lane), hi = bt32((unsigned)(X >> 32), lane);
+            if (lane < t)
+                dst[2 * lane + (warp & 1)] = lo;
+            if (lane + 32 < t)
+                dst[2 * (lane + 32) + (warp & 1)] = hi;
         }
     }
-    __syncwarp();
-    // row order of the window, P and Q
-    for (int i = lane; i < nwin; i += 32)
+    __syncthreads();
+    // maps for the sweep, by pivot column: row of M = U_J^-1 L^-1 (= (O_J)^-1: raw panel bits ->
+    // coordinates over the original pivot rows) and the row of U_J^-1 scattered to the pivot
+    // columns. Two threads per row of M, each over half of the inner index.
+    {
+        const int row = tid >> 1, half = tid & 1;
+        const u64 ua = row < t ? S.sUi[row] : 0ull;
+        u64 ma = 0;
+        const int kend = min(t, 32 * half + 32);
+        for (int k = 32 * half; k < kend; ++k)
+            ma ^= ((ua >> k) & 1ull) ? S.sLi[k] : 0ull;
+        ma ^= __shfl_xor_sync(GF2_FULL, ma, 1);
+        if (half == 0 && row < t) {
+            sXp[S.sPcol[row]] = ma;
+            sXm[S.sPcol[row]] = pdep64(ua, J);
+        }
+    }
+    __syncthreads();
+    // row order of the window, P and Q, the panel state
+    for (int i = tid; i < nwin; i += PIVOT_THREADS)
         perm[r + i] = S.Wph[i];
-    for (int s2 = lane; s2 < t; s2 += 32) {
+    for (int s2 = tid; s2 < t; s2 += PIVOT_THREADS) {
         if (P)
             P[r + s2] = S.sPpos[s2];
         if (Q)
             Q[r + s2] = 64ll * b + S.sPcol[s2];
-    }
-    // maps for the sweep, by pivot column: row of M = U_J^-1 L^-1 (= (O_J)^-1: raw panel bits ->
-    // coordinates over the original pivot rows) and the row of U_J^-1 scattered to the pivot columns
-    sXp[lane] = 0;
-    sXp[lane + 32] = 0;
-    sXm[lane] = 0;
-    sXm[lane + 32] = 0;
-    __syncwarp();
-    {
-        // rows lane, lane + 32 of M = U_J^-1 L^-1 (uniform loop: every lane reads the same L^-1 row)
-        const u64 ua = lane < t ? S.sUi[lane] : 0ull, ub = lane + 32 < t ? S.sUi[lane + 32] : 0ull;
-        u64 ma = 0, mb = 0;
-        for (int k = 0; k < t; ++k) {
-            const u64 lk = S.sLi[k];
-            ma ^= ((ua >> k) & 1ull) ? lk : 0ull;
-            mb ^= ((ub >> k) & 1ull) ? lk : 0ull;
-        }
-        if (lane < t) {
-            sXp[S.sPcol[lane]] = ma;
-            sXm[S.sPcol[lane]] = pdep64(ua, J);
-        }
-        if (lane + 32 < t) {
-            sXp[S.sPcol[lane + 32]] = mb;
-            sXm[S.sPcol[lane + 32]] = pdep64(ub, J);
-        }
-    }
-    __syncwarp();
-    for (int c = lane; c < 64; c += 32) {
-        st->zmap[c] = sXp[c];
-        st->xmap[c] = sXm[c];
-    }
-    for (int s2 = lane; s2 < t; s2 += 32) {
         st->prow[s2] = S.Wph[s2];
         st->pcol[s2] = S.sPcol[s2];
         st->newblk[s2] = S.sNew[s2];
         st->zpiv[s2] = S.sLi[s2];
     }
-    if (lane == 0) {
+    if (tid < 64) {
+        st->zmap[tid] = sXp[tid];
+        st->xmap[tid] = sXm[tid];
+    }
+    if (tid == 0) {
         st->r_cur = r;
         st->kbar = t;
         st->r_next = r + t;
@@ -653,7 +620,7 @@ __device__ __forceinline__ void pivot_panel(const u64 *__restrict__ side, int *_
     }
 }
 
-__global__ void __launch_bounds__(32, 1)
+__global__ void __launch_bounds__(PIVOT_THREADS, 1)
 k_pivot(const u64 *__restrict__ side, int *__restrict__ perm, const PanelState *__restrict__ st_prev, PanelState *st,
         int64_t *P, int64_t *Q, int m, int b, int nbits)
 {
@@ -1191,7 +1158,7 @@ __global__ void k_init_b(const gf2::ElimDesc *__restrict__ D)
     }
 }
 
-__global__ void __launch_bounds__(32, 1) k_pivot_b(const gf2::ElimDesc *__restrict__ D, const int *__restrict__ idx, int b)
+__global__ void __launch_bounds__(PIVOT_THREADS, 1) k_pivot_b(const gf2::ElimDesc *__restrict__ D, const int *__restrict__ idx, int b)
 {
     const gf2::ElimDesc &d = D[idx[blockIdx.x]];
     const int nbits = min(64, d.n - 64 * b);
@@ -1274,7 +1241,7 @@ int batch_pivot(const ElimDesc *D, const int *idx, int nact, int b, cudaStream_t
     if (nact <= 0)
         return GF2_OK;
     const int tok = prof_begin(s);
-    k_pivot_b<<<nact, 32, 0, s>>>(D, idx, b);
+    k_pivot_b<<<nact, PIVOT_THREADS, 0, s>>>(D, idx, b);
     prof_end(s, GF2_PROF_PIVOT, tok);
     prof_launched(1);
     return note_cuda(cudaGetLastError());
@@ -1410,7 +1377,7 @@ int elim_run(const Elim &e)
         u64 *nxt = e.side + (size_t)((b + 1) & 1) * e.m;
         PanelState *stb = e.st + (b & 1);
         int tok = prof_begin(e.s);
-        k_pivot<<<1, 32, 0, e.s>>>(cur, e.perm, e.st + ((b + 1) & 1), stb, e.P, e.Q, m, b, nbits);
+        k_pivot<<<1, PIVOT_THREADS, 0, e.s>>>(cur, e.perm, e.st + ((b + 1) & 1), stb, e.P, e.Q, m, b, nbits);
         prof_end(e.s, GF2_PROF_PIVOT, tok);
         prof_launched(1);
         if ((rc = note_cuda(cudaGetLastError())))
@@ -1423,7 +1390,7 @@ int elim_run(const Elim &e)
         if ((rc = note_cuda(cudaGetLastError())) || (rc = note_cuda(cudaEventRecord(ev_next, e.s))) ||
             (rc = note_cuda(cudaStreamWaitEvent(t, ev_next, 0))))
             return rc;
-        rc = e.tile_words == 4 ? launch_sweep<4, 4, 256, 2, true>(e, b, t) : launch_sweep<8, 2, 512, 1, true>(e, b, t);
+        rc = e.tile_words == 4 ? launch_sweep<4, 4, 256, 2, true>(e, b, t) : launch_sweep<8, 1, 1024, 1, true>(e, b, t);
         if (rc || (rc = note_cuda(cudaEventRecord(ev_rest, t))))
             return rc;
     }
