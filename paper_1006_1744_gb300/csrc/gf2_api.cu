@@ -49,8 +49,6 @@ ElimLayout elim_layout(int op, int64_t m, int64_t n)
     off = align_up(off + (size_t)2 * m * sizeof(u64), 256);
     L.pmask = off;
     off = align_up(off + (size_t)(W + 1) * sizeof(u64), 256);
-    L.tlist = off;
-    off = align_up(off + (size_t)m * sizeof(int), 256);
     L.out = off;
     off = align_up(off + (size_t)m * stride * sizeof(u64), 256);
     // Q (rref) or P,Q scratch (rank) share one area after `out`
@@ -169,7 +167,6 @@ static Elim make_elim(uint64_t *A, int64_t m, int64_t n, int64_t stride, char *w
     e.W = (n + 63) / 64;
     e.st = reinterpret_cast<PanelState *>(work + L.state);
     e.stf = final_state(e.st, e.W);
-    e.tlist = reinterpret_cast<int *>(work + L.tlist);
     e.perm = reinterpret_cast<int *>(work + L.perm);
     e.side = reinterpret_cast<u64 *>(work + L.side);
     e.pmask = reinterpret_cast<u64 *>(work + L.pmask);

@@ -31,6 +31,13 @@ struct PanelState {
     u64 zpiv[64];   // pivot t -> row t of L^-1: U_t as a sum of the ORIGINAL pivot rows O
     u64 zmap[64];   // column c -> row of (O_J)^-1 = U_J^-1 L^-1 for the pivot at c (0 elsewhere)
     u64 xmap[64];   // column c -> row of U_J^-1 for the pivot at c, scattered to the pivot columns
+    // Row-order changes of this panel, applied to the position -> row map by the
+    // next panel's pivot search (a sweep running meanwhile reads them from here):
+    int nwin;        // window positions r_cur .. r_cur + nwin - 1 ...
+    int nx;          // ... and nx positions past the window
+    int wperm[128];  // window position - r_cur -> physical row
+    int xpos[64];    // position past the window -> physical row xval
+    int xval[64];
 };
 
 // ---------------------------------------------------------------------------
@@ -123,7 +130,6 @@ struct ElimLayout {
     size_t perm;    // int32[m]: position -> physical row
     size_t side;    // u64[2][m]: panel word of each physical row (double buffered)
     size_t pmask;   // u64[W]: pivot-column mask
-    size_t tlist;   // int32[m]: physical rows of the trailing positions of the current panel
     size_t out;     // u64[m * stride]: rows in final order (pls / rref), or the copy (rank)
     size_t rref_b;  // rref: non-pivot part of S, compacted
     size_t rref_x;  // rref: solved non-pivot part
@@ -141,7 +147,6 @@ struct Elim {
     int64_t m, n, stride, W;
     PanelState *st;   // the two panel states
     PanelState *stf;  // final_state(st, W): rank and pivots after elim_run
-    int *tlist;
     int *perm;
     u64 *side;
     u64 *pmask;

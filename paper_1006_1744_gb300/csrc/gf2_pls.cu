@@ -38,6 +38,8 @@ __global__ void k_init(const uint64_t *__restrict__ A, int64_t stride, int *__re
             side0[i] = A[(int64_t)i * stride];
     }
     if (i < 2 && st) {  // both panel states
+        st[i].nwin = 0;
+        st[i].nx = 0;
         st[i].r_cur = 0;
         st[i].r_next = 0;
         st[i].kbar = 0;
@@ -88,19 +90,6 @@ __device__ __forceinline__ unsigned bt32(unsigned x, int lane)
     return x;
 }
 
-// exchange bits t (< 64) and p (< 128) of the 128-bit value (lo, hi)
-__device__ __forceinline__ void swap_rows128(u64 &lo, u64 &hi, int t, int p)
-{
-    if (p < 64) {
-        const u64 d = ((lo >> t) ^ (lo >> p)) & 1ull;
-        lo ^= (d << t) | (d << p);
-    } else {
-        const u64 d = ((lo >> t) ^ (hi >> (p - 64))) & 1ull;
-        lo ^= d << t;
-        hi ^= d << (p - 64);
-    }
-}
-
 struct PivotShared {
     // window, indexed by position - r (row form)
     u64 Ww[WIN], Wx[WIN];
@@ -115,10 +104,53 @@ struct PivotShared {
     u64 TVw[256], TVx[256];
     u64 gVw[GROUP], gVx[GROUP];
     int gIpos[GROUP], gX8[GROUP], gLinv[GROUP], gMm[GROUP], gUinv[GROUP];
+    // previous panel: its maps (raw panel bits -> coordinates) and its pivot rows' word b
+    u64 pZ[64], pO[64];
+    // positions past the window swapped in this panel (position -> physical row)
+    int nx;
+    int xpos[64], xval[64];
 };
 
-__device__ bool pivot_fast(const u64 *__restrict__ side, const int *__restrict__ perm, int r, int m, int nwin,
-                           int nbits, int &t_out, u64 &J_out, PivotShared &S)
+// Context for the panel word b of a row: the previous panel's sweep updates
+// word b only in its side buffer, so the pivot search derives it from A
+// (current up to panel b - 2) plus panel b - 1's contribution.
+struct WordCtx {
+    const uint64_t *A;
+    int64_t stride;
+    const u64 *side_prev;  // panel word b - 1 of every row (nullptr for b = 0)
+    int b;
+};
+
+__device__ __forceinline__ u64 panel_word(const WordCtx &c, const PivotShared &S, int ph)
+{
+    u64 w = c.A[(int64_t)ph * c.stride + c.b];
+    if (c.side_prev) {
+        u64 v = c.side_prev[ph], z = 0, acc = 0;
+        while (v) {
+            const int k = ctz64(v);
+            v &= v - 1;
+            z ^= S.pZ[k];
+        }
+        while (z) {
+            const int k = ctz64(z);
+            z &= z - 1;
+            acc ^= S.pO[k];
+        }
+        w ^= acc;
+    }
+    return w;
+}
+
+// position -> physical row during the pivot search (perm plus this panel's swaps past the window)
+__device__ __forceinline__ int perm_at(const int *__restrict__ perm, const PivotShared &S, int p)
+{
+    for (int x = 0; x < S.nx; ++x)
+        if (S.xpos[x] == p)
+            return S.xval[x];
+    return perm[p];
+}
+
+__device__ bool pivot_fast(int r, int m, int nwin, int nbits, int &t_out, u64 &J_out, PivotShared &S)
 {
     const int lane = threadIdx.x;
     // lane l holds the window rows at initial positions l + 32 k; a swap of positions
@@ -130,12 +162,11 @@ __device__ bool pivot_fast(const u64 *__restrict__ side, const int *__restrict__
     for (int k = 0; k < NSLOT; ++k) {
         const int i = lane + 32 * k;
         act[k] = i < nwin;
-        phys[k] = act[k] ? perm[r + i] : 0;
+        phys[k] = act[k] ? S.Wph[i] : 0;
+        row[k] = act[k] ? S.Ww[i] : 0ull;
         pos[k] = i;
     }
-#pragma unroll
-    for (int k = 0; k < NSLOT; ++k)
-        row[k] = act[k] ? side[phys[k]] : 0ull;
+    __syncwarp();
     // pivot s: lane s & 31 keeps its panel word, position (at the time of the step) and column
     u64 nw0 = 0, nw1 = 0;
     int recp0 = 0, recp1 = 0, recj0 = 0, recj1 = 0;
@@ -217,18 +248,14 @@ __device__ bool pivot_fast(const u64 *__restrict__ side, const int *__restrict__
 // them (a contiguous prefix of the row order, so a 1 found there is the first
 // one in its column), one at a time otherwise, with rows past the window
 // reduced from scratch by the Gauss-Jordan basis.
-__device__ void pivot_rows(const u64 *__restrict__ side, int *__restrict__ perm, int r, int m, int nwin, int nbits,
+__device__ void pivot_rows(const WordCtx &wc, const int *__restrict__ perm, int r, int m, int nwin, int nbits,
                            int &t_out, u64 &J_out, PivotShared &S)
 {
     const int lane = threadIdx.x;
     int t = 0;
     u64 J = 0;
-    for (int i = lane; i < nwin; i += 32) {
-        const int ph = perm[r + i];
-        S.Wph[i] = ph;
-        S.Ww[i] = side[ph];
+    for (int i = lane; i < nwin; i += 32)
         S.Wx[i] = 0;
-    }
     __syncwarp();
     int jlow = 0;
     while (nwin > 0 && t < 64 && jlow < nbits && r + t < m) {
@@ -430,8 +457,8 @@ __device__ void pivot_rows(const u64 *__restrict__ side, int *__restrict__ perm,
                 int c = 64, phh = -1;
                 u64 ww = 0, xx = 0;
                 if (p < m) {
-                    phh = perm[p];
-                    ww = side[phh];
+                    phh = perm_at(perm, S, p);
+                    ww = panel_word(wc, S, phh);
                     u64 pm = ww & J;
                     while (pm) {
                         const int cc = ctz64(pm);
@@ -464,7 +491,14 @@ __device__ void pivot_rows(const u64 *__restrict__ side, int *__restrict__ perm,
         }
         if (lane == 0) {
             if (from_out) {
-                perm[pos] = S.Wph[t];  // the head row takes the pivot's old position
+                // the head row takes the pivot's old position (recorded, applied later)
+                int x = 0;
+                while (x < S.nx && S.xpos[x] != pos)
+                    ++x;
+                S.xpos[x] = pos;
+                S.xval[x] = S.Wph[t];
+                if (x == S.nx)
+                    ++S.nx;
                 S.Ww[t] = ow;
                 S.Wx[t] = ox;
                 S.Wph[t] = oph;
@@ -520,7 +554,14 @@ __device__ void pivot_rows(const u64 *__restrict__ side, int *__restrict__ perm,
 
 constexpr int PIVOT_THREADS = 128;  // warp 0 runs the elimination chain; all four share the rest
 
-__device__ __forceinline__ void pivot_panel(const u64 *__restrict__ side, int *__restrict__ perm,
+// Pivot search of panel b. It first applies panel b - 1's row-order changes to
+// perm (no sweep reads those positions from perm), then forms the window: the
+// panel word b of the rows at positions r .. r + nwin - 1, from A plus panel
+// b - 1's contribution (side_prev = panel word b - 1 of every row; nullptr for
+// b = 0). This panel's own row-order changes go to st (nwin, wperm, nx, xpos,
+// xval) for the sweep of this panel and the pivot search of the next one.
+__device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int64_t stride,
+                                            const u64 *__restrict__ side_prev, int *__restrict__ perm,
                                             const PanelState *__restrict__ st_prev, PanelState *st, int64_t *P,
                                             int64_t *Q, int m, int b, int nbits)
 {
@@ -531,14 +572,35 @@ __device__ __forceinline__ void pivot_panel(const u64 *__restrict__ side, int *_
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = st_prev->r_next;
     const int nwin = (r < m && !st_prev->zero_tail) ? min(WIN, m - r) : 0;
+    const WordCtx wc{A, stride, b > 0 ? side_prev : nullptr, b};
+    if (b > 0) {
+        const int pr = st_prev->r_cur, pn = st_prev->nwin, px = st_prev->nx;
+        for (int i = tid; i < pn; i += PIVOT_THREADS)
+            perm[pr + i] = st_prev->wperm[i];
+        for (int x = tid; x < px; x += PIVOT_THREADS)
+            perm[st_prev->xpos[x]] = st_prev->xval[x];
+        if (tid < 64) {
+            S.pZ[tid] = st_prev->zmap[tid];
+            S.pO[tid] = tid < st_prev->kbar ? A[(int64_t)st_prev->prow[tid] * stride + b] : 0ull;
+        }
+    }
+    if (tid == 0)
+        S.nx = 0;
+    __syncthreads();
+    for (int i = tid; i < nwin; i += PIVOT_THREADS) {
+        const int ph = perm[r + i];
+        S.Wph[i] = ph;
+        S.Ww[i] = panel_word(wc, S, ph);
+    }
+    __syncthreads();
     if (warp == 0) {
         int t = 0, fast = 1;
         u64 J = 0;
         if (nwin > 0) {
-            fast = pivot_fast(side, perm, r, m, nwin, nbits, t, J, S) ? 1 : 0;
+            fast = pivot_fast(r, m, nwin, nbits, t, J, S) ? 1 : 0;
             __syncwarp();
             if (!fast)
-                pivot_rows(side, perm, r, m, nwin, nbits, t, J, S);
+                pivot_rows(wc, perm, r, m, nwin, nbits, t, J, S);
         }
         if (lane == 0) {
             sT = t;
@@ -595,9 +657,13 @@ __device__ __forceinline__ void pivot_panel(const u64 *__restrict__ side, int *_
         }
     }
     __syncthreads();
-    // row order of the window, P and Q, the panel state
+    // row order of the window (applied to perm by the next panel), P and Q, the panel state
     for (int i = tid; i < nwin; i += PIVOT_THREADS)
-        perm[r + i] = S.Wph[i];
+        st->wperm[i] = S.Wph[i];
+    for (int x = tid; x < S.nx; x += PIVOT_THREADS) {
+        st->xpos[x] = S.xpos[x];
+        st->xval[x] = S.xval[x];
+    }
     for (int s2 = tid; s2 < t; s2 += PIVOT_THREADS) {
         if (P)
             P[r + s2] = S.sPpos[s2];
@@ -617,14 +683,27 @@ __device__ __forceinline__ void pivot_panel(const u64 *__restrict__ side, int *_
         st->kbar = t;
         st->r_next = r + t;
         st->J = J;
+        st->nwin = nwin;
+        st->nx = S.nx;
     }
 }
 
-__global__ void __launch_bounds__(PIVOT_THREADS, 1)
-k_pivot(const u64 *__restrict__ side, int *__restrict__ perm, const PanelState *__restrict__ st_prev, PanelState *st,
-        int64_t *P, int64_t *Q, int m, int b, int nbits)
+// The last panel's row-order changes (before the final gather).
+__device__ __forceinline__ void apply_order(int *__restrict__ perm, const PanelState *__restrict__ st)
 {
-    pivot_panel(side, perm, st_prev, st, P, Q, m, b, nbits);
+    for (int i = threadIdx.x; i < st->nwin; i += blockDim.x)
+        perm[st->r_cur + i] = st->wperm[i];
+    for (int x = threadIdx.x; x < st->nx; x += blockDim.x)
+        perm[st->xpos[x]] = st->xval[x];
+}
+
+__global__ void k_apply_order(int *__restrict__ perm, const PanelState *__restrict__ st) { apply_order(perm, st); }
+
+__global__ void __launch_bounds__(PIVOT_THREADS, 1)
+k_pivot(const uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_prev, int *__restrict__ perm,
+        const PanelState *__restrict__ st_prev, PanelState *st, int64_t *P, int64_t *Q, int m, int b, int nbits)
+{
+    pivot_panel(A, stride, side_prev, perm, st_prev, st, P, Q, m, b, nbits);
 }
 
 // ---------------------------------------------------------------------------
@@ -645,16 +724,25 @@ k_pivot(const u64 *__restrict__ side, int *__restrict__ perm, const PanelState *
 // keeps its tables while consecutive work items share a tile, and keeps RPT
 // rows per thread in flight.
 // ---------------------------------------------------------------------------
-// REST = the look-ahead split: word b + 1 (the next panel's word) and the
-// next side buffer are left to next_panel, and the trailing rows come from the
-// list next_panel wrote (the row order may be changing under a concurrent
-// pivot search of panel b + 1).
-template <int TW, int RPT, int NT, bool REST>
+// physical row at trailing position p of the panel that st describes: its
+// window order, its swaps past the window, else perm (which the next panel's
+// pivot search may be rewriting meanwhile, at exactly those positions)
+__device__ __forceinline__ int trailing_row(const int *__restrict__ perm, const PanelState *__restrict__ st, int r,
+                                            int nwin, int nx, int p)
+{
+    if (p < r + nwin)
+        return st->wperm[p - r];
+    for (int x = 0; x < nx; ++x)
+        if (st->xpos[x] == p)
+            return st->xval[x];
+    return perm[p];
+}
+
+template <int TW, int RPT, int NT>
 __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_cur,
                                             u64 *__restrict__ side_nxt, const int *__restrict__ perm,
-                                            const int *__restrict__ tlist, const PanelState *__restrict__ st,
-                                            uint64_t *__restrict__ out, int64_t ostride, int m, int W, int b, int cta,
-                                            int ncta)
+                                            const PanelState *__restrict__ st, uint64_t *__restrict__ out,
+                                            int64_t ostride, int m, int W, int b, int cta, int ncta)
 {
     constexpr int TPR = TW / 2;     // threads per row, two words each
     constexpr int RPP = NT / TPR;   // rows per thread slot and pass
@@ -666,19 +754,19 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
     u64 *sO = sX + 8 * 256;       // [64][TW]      pivot rows, current tile
     u64 *sMap = sO + 64 * TW;     // [128]         zmap, xmap
 
-    const int r = st->r_cur, kbar = st->kbar;
+    const int r = st->r_cur, kbar = st->kbar, nwin = st->nwin, nx = st->nx;
     const int M = m - r;
     if (M <= 0)
         return;
     const int tid = threadIdx.x;
     if (kbar == 0) {
-        if (REST)
-            return;
-        if (b + 1 < W)
-            for (int p = r + cta * NT + tid; p < m; p += ncta * NT) {
-                int ph = perm[p];
+        // no pivot: every trailing row's panel word is zero; word b + 1 is unchanged
+        for (int p = r + cta * NT + tid; p < m; p += ncta * NT) {
+            const int ph = trailing_row(perm, st, r, nwin, nx, p);
+            A[(int64_t)ph * stride + b] = side_cur[ph];
+            if (b + 1 < W)
                 side_nxt[ph] = A[(int64_t)ph * stride + b + 1];
-            }
+        }
         return;
     }
     const int wstart = b & ~1;
@@ -762,7 +850,7 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
                 const int p = pb + j * RPP + rg;
                 valid[j] = p < p_end;
                 isp[j] = valid[j] && p < r + kbar;
-                ph[j] = !valid[j] ? 0 : (isp[j] ? st->prow[p - r] : (REST ? tlist[p - r - kbar] : perm[p]));
+                ph[j] = !valid[j] ? 0 : (isp[j] ? st->prow[p - r] : trailing_row(perm, st, r, nwin, nx, p));
             }
             // (b) their panel words and current words of the tile, all in flight
 #pragma unroll
@@ -816,9 +904,9 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
                     // pivot row t = p - r: final row U_t, written in final position
                     if (out) {
                         uint64_t *o = out + (int64_t)p * ostride;
-                        if (w0 >= b && !(REST && w0 == b + 1))
+                        if (w0 >= b)
                             o[w0] = (w0 == b) ? st->newblk[p - r] : acc0;
-                        if (two && !(REST && w0 + 1 == b + 1))
+                        if (two)
                             o[w0 + 1] = (w0 + 1 == b) ? st->newblk[p - r] : acc1;
                     }
                     continue;
@@ -839,11 +927,14 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
                     n0 ^= acc0;
                     n1 ^= acc1;
                 }
+                // word b + 1 goes only to the next side buffer: the next pivot search reads
+                // it in A (as it was before this panel) while this sweep runs, and the next
+                // panel's sweep writes that word's final value
                 uint64_t *a = A + (int64_t)ph[j] * stride + w0;
-                if (REST && w0 == b + 1) {
+                if (w0 == b + 1) {
                     if (two)
-                        a[1] = n1;  // word b + 1 belongs to next_panel
-                } else if (REST && w0 + 1 == b + 1) {
+                        a[1] = n1;
+                } else if (w0 + 1 == b + 1) {
                     a[0] = n0;
                 } else if (two) {
                     ulonglong2 v2;
@@ -853,7 +944,7 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
                 } else {
                     a[0] = n0;
                 }
-                if (!REST && b + 1 < W) {
+                if (b + 1 < W) {
                     if (w0 == b + 1)
                         side_nxt[ph[j]] = n0;
                     else if (two && w0 + 1 == b + 1)
@@ -864,109 +955,13 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
     }
 }
 
-template <int TW, int RPT, int NT, int MINB, bool REST>
+template <int TW, int RPT, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
 k_sweep(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_cur, u64 *__restrict__ side_nxt,
-        const int *__restrict__ perm, const int *__restrict__ tlist, const PanelState *__restrict__ st,
-        uint64_t *__restrict__ out, int64_t ostride, int m, int W, int b)
+        const int *__restrict__ perm, const PanelState *__restrict__ st, uint64_t *__restrict__ out, int64_t ostride,
+        int m, int W, int b)
 {
-    sweep_panel<TW, RPT, NT, REST>(A, stride, side_cur, side_nxt, perm, tlist, st, out, ostride, m, W, b, blockIdx.x,
-                               gridDim.x);
-}
-
-// ---------------------------------------------------------------------------
-// Look-ahead part of the sweep of panel b: word b + 1 only -- the word the
-// pivot search of panel b + 1 reads -- for every trailing row (also stored in
-// the next side buffer) and for the pivot rows (to `out`), with one Gray-code
-// table set over that single word. It also records the physical rows of the
-// trailing positions, so that the rest of the sweep never reads the row order
-// while the next pivot search changes it. One trailing row per thread.
-// ---------------------------------------------------------------------------
-constexpr int NEXT_THREADS = 256;
-
-__global__ void __launch_bounds__(NEXT_THREADS)
-k_next(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_cur, u64 *__restrict__ side_nxt,
-       const int *__restrict__ perm, int *__restrict__ tlist, const PanelState *__restrict__ st,
-       uint64_t *__restrict__ out, int64_t ostride, int m, int W, int b)
-{
-    __shared__ u64 sT1[8 * 256];  // sums of the pivot rows' word b + 1, one table per 8 pivots
-    __shared__ u64 sZ1[8 * 256];  // raw panel byte -> coordinates over the pivot rows
-    __shared__ u64 sO1[64];
-    __shared__ u64 sMap1[64];
-    const int r = st->r_cur, kbar = st->kbar;
-    const int p0 = r + kbar;  // first trailing position
-    const int tid = threadIdx.x;
-    const int g0 = blockIdx.x * NEXT_THREADS + tid, gs = gridDim.x * NEXT_THREADS;
-    const bool has_next = b + 1 < W;
-    if (kbar == 0) {
-        for (int p = p0 + g0; p < m; p += gs) {
-            const int ph = perm[p];
-            tlist[p - p0] = ph;
-            if (has_next)
-                side_nxt[ph] = A[(int64_t)ph * stride + b + 1];
-        }
-        return;
-    }
-    if (tid < 64) {
-        sMap1[tid] = st->zmap[tid];
-        sO1[tid] = (has_next && tid < kbar) ? A[(int64_t)st->prow[tid] * stride + b + 1] : 0ull;
-    }
-    __syncthreads();
-    for (int e = tid; e < 8 * 256; e += NEXT_THREADS) {
-        const int q = e >> 8, v = e & 255;
-        u64 zz = 0;
-#pragma unroll
-        for (int bit = 0; bit < 8; ++bit)
-            if ((v >> bit) & 1)
-                zz ^= sMap1[8 * q + bit];
-        sZ1[e] = zz;
-    }
-    const int ng = (kbar + 7) >> 3;
-    // Gray-code enumeration: T[hi << 4 | gray(i)] from T[hi << 4 | gray(i - 1)] by one row
-    for (int e = tid; e < ng * 16; e += NEXT_THREADS) {
-        const int vh = e & 15, g = e >> 4;
-        const u64 *Og = sO1 + 8 * g;
-        u64 cur = 0;
-#pragma unroll
-        for (int bit = 0; bit < 4; ++bit)
-            if ((vh >> bit) & 1)
-                cur ^= Og[4 + bit];
-        u64 *Tg = sT1 + g * 256 + (vh << 4);
-        Tg[0] = cur;
-#pragma unroll
-        for (int i = 1; i < 16; ++i) {
-            cur ^= Og[__ffs(i) - 1];
-            Tg[i ^ (i >> 1)] = cur;
-        }
-    }
-    __syncthreads();
-    for (int p = p0 + g0; p < m; p += gs) {
-        const int ph = perm[p];
-        tlist[p - p0] = ph;
-        if (!has_next)
-            continue;
-        const u64 wv = side_cur[ph];
-        uint64_t *a = A + (int64_t)ph * stride + b + 1;
-        const u64 old = *a;
-        u64 z = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            z ^= sZ1[(q << 8) | (int)((wv >> (8 * q)) & 255ull)];
-        u64 acc = 0;
-        for (int g = 0; g < ng; ++g)
-            acc ^= sT1[g * 256 + (int)((z >> (8 * g)) & 255ull)];
-        const u64 nw = old ^ acc;
-        *a = nw;
-        side_nxt[ph] = nw;
-    }
-    if (has_next && out)
-        for (int s2 = g0; s2 < kbar; s2 += gs) {
-            const u64 z = st->zpiv[s2];
-            u64 acc = 0;
-            for (int g = 0; g < ng; ++g)
-                acc ^= sT1[g * 256 + (int)((z >> (8 * g)) & 255ull)];
-            out[(int64_t)(r + s2) * ostride + b + 1] = acc;
-        }
+    sweep_panel<TW, RPT, NT>(A, stride, side_cur, side_nxt, perm, st, out, ostride, m, W, b, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1111,14 +1106,14 @@ constexpr size_t sweep_smem()
     return (size_t)(8 * 256 * TW + 2 * 8 * 256 + 64 * TW + 128) * sizeof(u64);
 }
 
-template <int TW, int RPT, int NT, int MINB, bool REST>
+template <int TW, int RPT, int NT, int MINB>
 int launch_sweep(const gf2::Elim &e, int b, cudaStream_t s)
 {
     static bool attr_set = false;  // per process; the attribute is per function
     constexpr size_t smem = sweep_smem<TW>();
     if (!attr_set) {
-        cudaError_t err = cudaFuncSetAttribute(k_sweep<TW, RPT, NT, MINB, REST>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t err =
+            cudaFuncSetAttribute(k_sweep<TW, RPT, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess)
             return gf2::note_cuda(err);
         attr_set = true;
@@ -1126,9 +1121,8 @@ int launch_sweep(const gf2::Elim &e, int b, cudaStream_t s)
     const u64 *cur = e.side + (size_t)(b & 1) * e.m;
     u64 *nxt = e.side + (size_t)((b + 1) & 1) * e.m;
     const int tok = gf2::prof_begin(s);
-    k_sweep<TW, RPT, NT, MINB, REST><<<e.grid * MINB, NT, smem, s>>>(e.A, e.stride, cur, nxt, e.perm, e.tlist,
-                                                                   e.st + (b & 1), e.out, e.ostride, (int)e.m,
-                                                                   (int)e.W, b);
+    k_sweep<TW, RPT, NT, MINB><<<e.grid * MINB, NT, smem, s>>>(e.A, e.stride, cur, nxt, e.perm, e.st + (b & 1), e.out,
+                                                               e.ostride, (int)e.m, (int)e.W, b);
     gf2::prof_end(s, GF2_PROF_SWEEP, tok);
     gf2::prof_launched(1);
     return gf2::note_cuda(cudaGetLastError());
@@ -1149,6 +1143,8 @@ __global__ void k_init_b(const gf2::ElimDesc *__restrict__ D)
     for (int w = g; w < d.W + 1; w += nt)
         d.pmask[w] = 0;
     if (g < 2) {
+        d.st[g].nwin = 0;
+        d.st[g].nx = 0;
         d.st[g].r_cur = 0;
         d.st[g].r_next = 0;
         d.st[g].kbar = 0;
@@ -1162,7 +1158,8 @@ __global__ void __launch_bounds__(PIVOT_THREADS, 1) k_pivot_b(const gf2::ElimDes
 {
     const gf2::ElimDesc &d = D[idx[blockIdx.x]];
     const int nbits = min(64, d.n - 64 * b);
-    pivot_panel(d.side + (size_t)(b & 1) * d.m, d.perm, d.st + ((b + 1) & 1), d.st + (b & 1), d.P, d.Q, d.m, b, nbits);
+    pivot_panel(d.A, d.stride, d.side + (size_t)((b + 1) & 1) * d.m, d.perm, d.st + ((b + 1) & 1), d.st + (b & 1),
+                d.P, d.Q, d.m, b, nbits);
 }
 
 template <int TW, int RPT, int MINB>
@@ -1179,9 +1176,15 @@ k_sweep_b(const gf2::ElimDesc *__restrict__ D, const int *__restrict__ idx, cons
             hi = mid - 1;
     }
     const gf2::ElimDesc &d = D[idx[lo]];
-    sweep_panel<TW, RPT, 256, false>(d.A, d.stride, d.side + (size_t)(b & 1) * d.m, d.side + (size_t)((b + 1) & 1) * d.m,
-                                d.perm, nullptr, d.st + (b & 1), d.out, d.ostride, d.m, d.W, b,
-                                (int)blockIdx.x - pre[lo], pre[lo + 1] - pre[lo]);
+    sweep_panel<TW, RPT, 256>(d.A, d.stride, d.side + (size_t)(b & 1) * d.m, d.side + (size_t)((b + 1) & 1) * d.m,
+                              d.perm, d.st + (b & 1), d.out, d.ostride, d.m, d.W, b, (int)blockIdx.x - pre[lo],
+                              pre[lo + 1] - pre[lo]);
+}
+
+__global__ void k_apply_order_b(const gf2::ElimDesc *__restrict__ D)
+{
+    const gf2::ElimDesc &d = D[blockIdx.y];
+    apply_order(d.perm, gf2::final_state(d.st, d.W));
 }
 
 __global__ void k_gather_b(const gf2::ElimDesc *__restrict__ D)
@@ -1281,11 +1284,12 @@ int batch_finish(const ElimDesc *D, int count, int max_m, cudaStream_t s)
     if (count <= 0)
         return GF2_OK;
     const unsigned gx = (unsigned)((max_m + 127) / 128 > 0 ? (max_m + 127) / 128 : 1);
+    k_apply_order_b<<<dim3(1, (unsigned)count), 128, 0, s>>>(D);
     k_gather_b<<<dim3(gx < 8 ? gx : 8, (unsigned)count), 256, 0, s>>>(D);
     k_pmask_b<<<dim3(1, (unsigned)count), 256, 0, s>>>(D);
     k_compress_b<<<dim3(gx, (unsigned)count), 128, 0, s>>>(D);
     k_copyback_b<<<dim3(gx < 16 ? gx : 16, (unsigned)count), 256, 0, s>>>(D);
-    prof_launched(4);
+    prof_launched(5);
     return note_cuda(cudaGetLastError());
 }
 
@@ -1349,12 +1353,12 @@ struct EventSet {
     }
 };
 
-// Panel elimination with a look-ahead of one panel. Panel b: the pivot search
-// (stream s), then the sweep's word b + 1 and trailing-row list (k_next, s),
-// then the rest of the sweep on the side stream t, which runs while the pivot
-// search of panel b + 1 proceeds on s. k_next of panel b + 1 waits for the rest
-// of panel b (both write words >= b + 2 of the same rows). Panel states and
-// side buffers alternate with the parity of b.
+// Panel elimination with a look-ahead of one panel. The pivot searches run on
+// stream s, the table sweeps on the side stream t: the sweep of panel b starts
+// when the pivot search of panel b is done and overlaps the pivot search of
+// panel b + 1, which derives its window from A (current up to panel b - 1, so
+// it waits for the sweep of panel b - 1) plus panel b's contribution. Panel
+// states and side buffers alternate with the parity of b.
 int elim_run(const Elim &e)
 {
     const int m = (int)e.m;
@@ -1367,34 +1371,31 @@ int elim_run(const Elim &e)
     EventSet E;
     if ((rc = side_stream(&t)) || (rc = E.create()))
         return rc;
-    cudaEvent_t ev_fork = E.ev[0], ev_next = E.ev[1], ev_rest = E.ev[2];
-    if ((rc = note_cuda(cudaEventRecord(ev_fork, e.s))) || (rc = note_cuda(cudaStreamWaitEvent(t, ev_fork, 0))))
-        return rc;
-    const int next_ctas = std::max(1, std::min((m + NEXT_THREADS - 1) / NEXT_THREADS, 2 * sm_count()));
+    cudaEvent_t ev_piv = E.ev[0], ev_rest[2] = {E.ev[1], E.ev[2]};
     for (int b = 0; b < (int)e.W; ++b) {
         const int nbits = (int)((e.n - 64ll * b) < 64 ? (e.n - 64ll * b) : 64);
-        const u64 *cur = e.side + (size_t)(b & 1) * e.m;
-        u64 *nxt = e.side + (size_t)((b + 1) & 1) * e.m;
+        const u64 *prev = e.side + (size_t)((b + 1) & 1) * e.m;  // panel word b - 1 of every row
         PanelState *stb = e.st + (b & 1);
-        int tok = prof_begin(e.s);
-        k_pivot<<<1, PIVOT_THREADS, 0, e.s>>>(cur, e.perm, e.st + ((b + 1) & 1), stb, e.P, e.Q, m, b, nbits);
+        if (b >= 2 && (rc = note_cuda(cudaStreamWaitEvent(e.s, ev_rest[b & 1], 0))))
+            return rc;
+        const int tok = prof_begin(e.s);
+        k_pivot<<<1, PIVOT_THREADS, 0, e.s>>>(e.A, e.stride, prev, e.perm, e.st + ((b + 1) & 1), stb, e.P, e.Q, m, b,
+                                              nbits);
         prof_end(e.s, GF2_PROF_PIVOT, tok);
         prof_launched(1);
-        if ((rc = note_cuda(cudaGetLastError())))
+        if ((rc = note_cuda(cudaGetLastError())) || (rc = note_cuda(cudaEventRecord(ev_piv, e.s))) ||
+            (rc = note_cuda(cudaStreamWaitEvent(t, ev_piv, 0))))
             return rc;
-        if (b > 0 && (rc = note_cuda(cudaStreamWaitEvent(e.s, ev_rest, 0))))
-            return rc;
-        k_next<<<next_ctas, NEXT_THREADS, 0, e.s>>>(e.A, e.stride, cur, nxt, e.perm, e.tlist, stb, e.out, e.ostride, m,
-                                                  (int)e.W, b);
-        prof_launched(1);
-        if ((rc = note_cuda(cudaGetLastError())) || (rc = note_cuda(cudaEventRecord(ev_next, e.s))) ||
-            (rc = note_cuda(cudaStreamWaitEvent(t, ev_next, 0))))
-            return rc;
-        rc = e.tile_words == 4 ? launch_sweep<4, 4, 256, 2, true>(e, b, t) : launch_sweep<8, 1, 1024, 1, true>(e, b, t);
-        if (rc || (rc = note_cuda(cudaEventRecord(ev_rest, t))))
+        rc = e.tile_words == 4 ? launch_sweep<4, 4, 256, 2>(e, b, t) : launch_sweep<8, 1, 1024, 1>(e, b, t);
+        if (rc || (rc = note_cuda(cudaEventRecord(ev_rest[b & 1], t))))
             return rc;
     }
-    return note_cuda(cudaStreamWaitEvent(e.s, ev_rest, 0));
+    // the last panel's row order, then wait for the last sweep
+    k_apply_order<<<1, 128, 0, e.s>>>(e.perm, e.stf);
+    prof_launched(1);
+    if ((rc = note_cuda(cudaGetLastError())))
+        return rc;
+    return note_cuda(cudaStreamWaitEvent(e.s, ev_rest[(e.W - 1) & 1], 0));
 }
 
 int elim_gather(const Elim &e, int64_t *rank)
