@@ -144,7 +144,7 @@ int check_opts(const gf2_opts *o)
         return GF2_OK;
     if (o->k != 0 && o->k != 8)
         return GF2_EINVAL;
-    if (o->tile_words != 0 && o->tile_words != 4 && o->tile_words != 8)
+    if (o->tile_words != 0 && o->tile_words != 4 && o->tile_words != 8 && o->tile_words != 16)
         return GF2_EINVAL;
     if (o->grid_ctas < 0 || o->product < 0 || o->product > 2 || o->cutoff_cols < 0)
         return GF2_EINVAL;
@@ -175,7 +175,7 @@ static Elim make_elim(uint64_t *A, int64_t m, int64_t n, int64_t stride, char *w
     e.P = P;
     e.Q = Q;
     e.s = s;
-    e.tile_words = (o && o->tile_words) ? o->tile_words : 8;
+    e.tile_words = (o && o->tile_words) ? o->tile_words : 16;
     e.grid = (o && o->grid_ctas) ? o->grid_ctas : sm_count();
     return e;
 }

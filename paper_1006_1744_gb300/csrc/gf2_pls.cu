@@ -104,8 +104,11 @@ struct PivotShared {
     u64 TVw[256], TVx[256];
     u64 gVw[GROUP], gVx[GROUP];
     int gIpos[GROUP], gX8[GROUP], gLinv[GROUP], gMm[GROUP], gUinv[GROUP];
-    // previous panel: its maps (raw panel bits -> coordinates) and its pivot rows' word b
+    // previous panel: its maps (raw panel bits -> coordinates) and its pivot rows' word b,
+    // as 4-bit tables: pNZ[q][v] = sum of the maps of the set bits of v at bits 4q..4q+3,
+    // pNO[q][v] likewise over the pivot rows
     u64 pZ[64], pO[64];
+    u64 pNZ[16][16], pNO[16][16];
     // positions past the window swapped in this panel (position -> physical row)
     int nx;
     int xpos[64], xval[64];
@@ -121,24 +124,23 @@ struct WordCtx {
     int b;
 };
 
+// word b of a row from its value in A and its panel word b - 1 (v)
+__device__ __forceinline__ u64 word_after(const PivotShared &S, u64 w, u64 v)
+{
+    u64 z = 0, acc = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+        z ^= S.pNZ[q][(int)((v >> (4 * q)) & 15ull)];
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+        acc ^= S.pNO[q][(int)((z >> (4 * q)) & 15ull)];
+    return w ^ acc;
+}
+
 __device__ __forceinline__ u64 panel_word(const WordCtx &c, const PivotShared &S, int ph)
 {
-    u64 w = c.A[(int64_t)ph * c.stride + c.b];
-    if (c.side_prev) {
-        u64 v = c.side_prev[ph], z = 0, acc = 0;
-        while (v) {
-            const int k = ctz64(v);
-            v &= v - 1;
-            z ^= S.pZ[k];
-        }
-        while (z) {
-            const int k = ctz64(z);
-            z &= z - 1;
-            acc ^= S.pO[k];
-        }
-        w ^= acc;
-    }
-    return w;
+    const u64 w = c.A[(int64_t)ph * c.stride + c.b];
+    return c.side_prev ? word_after(S, w, c.side_prev[ph]) : w;
 }
 
 // position -> physical row during the pivot search (perm plus this panel's swaps past the window)
@@ -553,6 +555,7 @@ __device__ void pivot_rows(const WordCtx &wc, const int *__restrict__ perm, int 
 }
 
 constexpr int PIVOT_THREADS = 128;  // warp 0 runs the elimination chain; all four share the rest
+static_assert(WIN <= PIVOT_THREADS, "one window row per thread when the window is formed");
 
 // Pivot search of panel b. It first applies panel b - 1's row-order changes to
 // perm (no sweep reads those positions from perm), then forms the window: the
@@ -573,24 +576,55 @@ __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int6
     const int r = st_prev->r_next;
     const int nwin = (r < m && !st_prev->zero_tail) ? min(WIN, m - r) : 0;
     const WordCtx wc{A, stride, b > 0 ? side_prev : nullptr, b};
-    if (b > 0) {
-        const int pr = st_prev->r_cur, pn = st_prev->nwin, px = st_prev->nx;
+    // window rows: the previous panel's order where it changed it, perm elsewhere
+    // (one row per thread; nwin <= PIVOT_THREADS)
+    int ph = 0;
+    u64 w = 0, v = 0;
+    {
+        const int pr = b > 0 ? st_prev->r_cur : 0, pn = b > 0 ? st_prev->nwin : 0, px = b > 0 ? st_prev->nx : 0;
+        if (tid < nwin) {
+            const int p = r + tid;
+            if (p < pr + pn) {
+                ph = st_prev->wperm[p - pr];
+            } else {
+                ph = -1;
+                for (int x = 0; x < px; ++x)
+                    if (st_prev->xpos[x] == p)
+                        ph = st_prev->xval[x];
+                if (ph < 0)
+                    ph = perm[p];
+            }
+            w = A[(int64_t)ph * stride + b];
+            if (b > 0)
+                v = side_prev[ph];
+        }
+        // apply the previous panel's order to perm (no sweep reads these positions from perm)
         for (int i = tid; i < pn; i += PIVOT_THREADS)
             perm[pr + i] = st_prev->wperm[i];
         for (int x = tid; x < px; x += PIVOT_THREADS)
             perm[st_prev->xpos[x]] = st_prev->xval[x];
-        if (tid < 64) {
-            S.pZ[tid] = st_prev->zmap[tid];
-            S.pO[tid] = tid < st_prev->kbar ? A[(int64_t)st_prev->prow[tid] * stride + b] : 0ull;
-        }
+    }
+    if (b > 0 && tid < 64) {
+        S.pZ[tid] = st_prev->zmap[tid];
+        S.pO[tid] = tid < st_prev->kbar ? A[(int64_t)st_prev->prow[tid] * stride + b] : 0ull;
     }
     if (tid == 0)
         S.nx = 0;
     __syncthreads();
-    for (int i = tid; i < nwin; i += PIVOT_THREADS) {
-        const int ph = perm[r + i];
-        S.Wph[i] = ph;
-        S.Ww[i] = panel_word(wc, S, ph);
+    if (b > 0)
+        for (int e = tid; e < 2 * 256; e += PIVOT_THREADS) {
+            const int which = e >> 8, q = (e >> 4) & 15, vv = e & 15;
+            const u64 *src = which ? S.pO : S.pZ;
+            u64 x = 0;
+#pragma unroll
+            for (int bit = 0; bit < 4; ++bit)
+                x ^= ((vv >> bit) & 1) ? src[4 * q + bit] : 0ull;
+            (which ? S.pNO : S.pNZ)[q][vv] = x;
+        }
+    __syncthreads();
+    if (tid < nwin) {
+        S.Wph[tid] = ph;
+        S.Ww[tid] = b > 0 ? word_after(S, w, v) : w;
     }
     __syncthreads();
     if (warp == 0) {
@@ -747,12 +781,19 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
     constexpr int TPR = TW / 2;     // threads per row, two words each
     constexpr int RPP = NT / TPR;   // rows per thread slot and pass
     constexpr int BPL = 8 / TPR;    // z-table bytes per thread
+    // HALF (16-word tiles, 128-byte table rows: a quarter-warp reads one whole
+    // row, so lookups never hit the same bank twice): each 8-bit table keeps only
+    // the sums of its first 7 rows, and one more table holds the sums of the 8
+    // tables' last rows, indexed by bit 7 of every byte of z.
+    constexpr bool HALF = TW == 16;
+    constexpr int TE = HALF ? 128 : 256;  // entries per 8-bit table
     extern __shared__ __align__(16) u64 sm[];
-    u64 *sT = sm;                 // [8][256][TW]  Gray-code tables of the pivot rows O
-    u64 *sZ = sT + 8 * 256 * TW;  // [8][256]      raw panel byte -> coordinates z
-    u64 *sX = sZ + 8 * 256;       // [8][256]      raw panel byte -> new panel word
-    u64 *sO = sX + 8 * 256;       // [64][TW]      pivot rows, current tile
-    u64 *sMap = sO + 64 * TW;     // [128]         zmap, xmap
+    u64 *sT = sm;                          // [8][TE][TW] Gray-code tables of the pivot rows O
+    u64 *sU = sT + 8 * TE * TW;            // [256][TW]   (HALF) sums of the rows 8 g + 7
+    u64 *sZ = sU + (HALF ? 256 * TW : 0);  // [8][256]    raw panel byte -> coordinates z
+    u64 *sX = sZ + 8 * 256;                // [8][256]    raw panel byte -> new panel word
+    u64 *sO = sX + 8 * 256;                // [64][TW]    pivot rows, current tile
+    u64 *sMap = sO + 64 * TW;              // [128]       zmap, xmap
 
     const int r = st->r_cur, kbar = st->kbar, nwin = st->nwin, nx = st->nx;
     const int M = m - r;
@@ -816,15 +857,17 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
                 sO[e] = v;
             }
             __syncthreads();
-            for (int e = tid; e < ng * TW * 16; e += NT) {
-                const int vh = e & 15, gw = e >> 4, wi = gw % TW, g = gw / TW;
+            // MakeTable: entry hi << 4 | gray(i) from entry hi << 4 | gray(i - 1) by one row
+            constexpr int HIB = HALF ? 3 : 4;  // high bits enumerated directly
+            for (int e = tid; e < ng * TW * (1 << HIB); e += NT) {
+                const int vh = e & ((1 << HIB) - 1), gw = e >> HIB, wi = gw % TW, g = gw / TW;
                 const u64 *Og = sO + (8 * g) * TW + wi;
                 u64 cur = 0;
 #pragma unroll
-                for (int bit = 0; bit < 4; ++bit)
+                for (int bit = 0; bit < HIB; ++bit)
                     if ((vh >> bit) & 1)
                         cur ^= Og[(4 + bit) * TW];
-                u64 *Tg = sT + (g * 256 + (vh << 4)) * TW + wi;
+                u64 *Tg = sT + (g * TE + (vh << 4)) * TW + wi;
                 Tg[0] = cur;
 #pragma unroll
                 for (int i = 1; i < 16; ++i) {
@@ -832,6 +875,23 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
                     Tg[(i ^ (i >> 1)) * TW] = cur;
                 }
             }
+            if (HALF)
+                for (int e = tid; e < TW * 16; e += NT) {
+                    const int vh = e & 15, wi = e >> 4;
+                    const u64 *O7 = sO + 7 * TW + wi;  // row 8 g + 7 at O7[8 g TW]
+                    u64 cur = 0;
+#pragma unroll
+                    for (int bit = 0; bit < 4; ++bit)
+                        if ((vh >> bit) & 1)
+                            cur ^= O7[8 * (4 + bit) * TW];
+                    u64 *Ug = sU + (vh << 4) * TW + wi;
+                    Ug[0] = cur;
+#pragma unroll
+                    for (int i = 1; i < 16; ++i) {
+                        cur ^= O7[8 * (__ffs(i) - 1) * TW];
+                        Ug[(i ^ (i >> 1)) * TW] = cur;
+                    }
+                }
             __syncthreads();
             cur_tile = tile;
         }
@@ -892,11 +952,20 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
 #pragma unroll
                 for (int g = 0; g < 8; ++g) {
                     if (g < ng) {
-                        const int v = (int)((zw[g >> 2] >> (8 * (g & 3))) & 255u);
-                        const ulonglong2 e2 = *reinterpret_cast<const ulonglong2 *>(tb0 + (g * 256 + v) * TW);
+                        const int v = (int)((zw[g >> 2] >> (8 * (g & 3))) & (TE - 1u));
+                        const ulonglong2 e2 = *reinterpret_cast<const ulonglong2 *>(tb0 + (g * TE + v) * TW);
                         acc0 ^= e2.x;
                         acc1 ^= e2.y;
                     }
+                }
+                if (HALF) {
+                    // bits 7, 15, ..., 63 of z gathered into one byte
+                    const unsigned top = ((((zw[0] >> 7) & 0x01010101u) * 0x01020408u) >> 24) |
+                                         (((((zw[1] >> 7) & 0x01010101u) * 0x01020408u) >> 24) << 4);
+                    const ulonglong2 e2 =
+                        *reinterpret_cast<const ulonglong2 *>(sU + (int)(top & 255u) * TW + 2 * sub);
+                    acc0 ^= e2.x;
+                    acc1 ^= e2.y;
                 }
                 if (!valid[j] || !wact)
                     continue;
@@ -1103,7 +1172,8 @@ __global__ void k_identity(int64_t *P, int64_t m, int64_t *Q, int64_t n, int64_t
 template <int TW>
 constexpr size_t sweep_smem()
 {
-    return (size_t)(8 * 256 * TW + 2 * 8 * 256 + 64 * TW + 128) * sizeof(u64);
+    return (TW == 16 ? (size_t)(8 * 128 * TW + 256 * TW) : (size_t)(8 * 256 * TW)) * sizeof(u64) +
+           (size_t)(2 * 8 * 256 + 64 * TW + 128) * sizeof(u64);
 }
 
 template <int TW, int RPT, int NT, int MINB>
@@ -1386,7 +1456,9 @@ int elim_run(const Elim &e)
         if ((rc = note_cuda(cudaGetLastError())) || (rc = note_cuda(cudaEventRecord(ev_piv, e.s))) ||
             (rc = note_cuda(cudaStreamWaitEvent(t, ev_piv, 0))))
             return rc;
-        rc = e.tile_words == 4 ? launch_sweep<4, 4, 256, 2>(e, b, t) : launch_sweep<8, 1, 1024, 1>(e, b, t);
+        rc = e.tile_words == 4   ? launch_sweep<4, 4, 256, 2>(e, b, t)
+             : e.tile_words == 8 ? launch_sweep<8, 1, 1024, 1>(e, b, t)
+                                 : launch_sweep<16, 1, 1024, 1>(e, b, t);
         if (rc || (rc = note_cuda(cudaEventRecord(ev_rest[b & 1], t))))
             return rc;
     }

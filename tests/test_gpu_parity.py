@@ -67,7 +67,7 @@ def test_pls_parity_config1_many_seeds(g):
         check_pls(g, A, 1024, 1024, opts={"k": 8})
 
 
-@pytest.mark.parametrize("tile", [4, 8])
+@pytest.mark.parametrize("tile", [4, 8, 16])
 def test_pls_parity_tile_and_grid_choices(g, tile):
     for grid in (1, 3, 152, 400):
         A = make("sparse05", 600, 900, grid)
