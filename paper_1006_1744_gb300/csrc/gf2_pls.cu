@@ -772,6 +772,47 @@ __device__ __forceinline__ int trailing_row(const int *__restrict__ perm, const 
     return perm[p];
 }
 
+// rows of one pass of the sweep: position -> physical row, pivot row or not, in range
+template <int RPT, int RPP>
+__device__ __forceinline__ void pass_rows(int pb, int rg, int p_end, int r, int kbar, int nwin, int nx,
+                                          const PanelState *__restrict__ st, const int *__restrict__ perm,
+                                          int (&ph)[RPT], bool (&valid)[RPT], bool (&isp)[RPT])
+{
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        const int p = pb + j * RPP + rg;
+        valid[j] = p < p_end;
+        isp[j] = valid[j] && p < r + kbar;
+        ph[j] = !valid[j] ? 0 : (isp[j] ? st->prow[p - r] : trailing_row(perm, st, r, nwin, nx, p));
+    }
+}
+
+// their panel words and their current words of the tile (not needed for pivot rows)
+template <int RPT>
+__device__ __forceinline__ void pass_loads(const uint64_t *__restrict__ A, int64_t stride,
+                                           const u64 *__restrict__ side_cur, int w0, bool two, bool wact,
+                                           const int (&ph)[RPT], const bool (&valid)[RPT], const bool (&isp)[RPT],
+                                           u64 (&wv)[RPT], u64 (&o0)[RPT], u64 (&o1)[RPT])
+{
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        const bool live = valid[j] && !isp[j];
+        wv[j] = live ? side_cur[ph[j]] : 0ull;
+        o0[j] = 0;
+        o1[j] = 0;
+        if (live && wact) {
+            const uint64_t *a = A + (int64_t)ph[j] * stride + w0;
+            if (two) {
+                const ulonglong2 v2 = *reinterpret_cast<const ulonglong2 *>(a);
+                o0[j] = v2.x;
+                o1[j] = v2.y;
+            } else {
+                o0[j] = a[0];
+            }
+        }
+    }
+}
+
 template <int TW, int RPT, int NT>
 __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_cur,
                                             u64 *__restrict__ side_nxt, const int *__restrict__ perm,
@@ -860,7 +901,8 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
             // MakeTable: entry hi << 4 | gray(i) from entry hi << 4 | gray(i - 1) by one row
             constexpr int HIB = HALF ? 3 : 4;  // high bits enumerated directly
             for (int e = tid; e < ng * TW * (1 << HIB); e += NT) {
-                const int vh = e & ((1 << HIB) - 1), gw = e >> HIB, wi = gw % TW, g = gw / TW;
+                // word index fastest: the lanes of a warp store to consecutive words
+                const int wi = e % TW, rest = e / TW, vh = rest & ((1 << HIB) - 1), g = rest >> HIB;
                 const u64 *Og = sO + (8 * g) * TW + wi;
                 u64 cur = 0;
 #pragma unroll
@@ -877,7 +919,7 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
             }
             if (HALF)
                 for (int e = tid; e < TW * 16; e += NT) {
-                    const int vh = e & 15, wi = e >> 4;
+                    const int wi = e % TW, vh = e / TW;
                     const u64 *O7 = sO + 7 * TW + wi;  // row 8 g + 7 at O7[8 g TW]
                     u64 cur = 0;
 #pragma unroll
@@ -900,36 +942,17 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
         const int w0 = wbase + 2 * sub;
         const bool two = w0 + 1 < W;
         const bool wact = w0 < W;
+        // software pipeline over passes: the physical rows of the pass after next and
+        // the words of the next pass are in flight while this pass is computed
+        int ph[RPT], phB[RPT], phC[RPT];
+        bool valid[RPT], validB[RPT], validC[RPT], isp[RPT], ispB[RPT], ispC[RPT];
+        u64 wv[RPT], o0[RPT], o1[RPT], wvB[RPT], o0B[RPT], o1B[RPT];
+        pass_rows<RPT, RPP>(p_begin, rg, p_end, r, kbar, nwin, nx, st, perm, ph, valid, isp);
+        pass_loads<RPT>(A, stride, side_cur, w0, two, wact, ph, valid, isp, wv, o0, o1);
+        pass_rows<RPT, RPP>(p_begin + PASS, rg, p_end, r, kbar, nwin, nx, st, perm, phB, validB, ispB);
         for (int pb = p_begin; pb < p_end; pb += PASS) {
-            int ph[RPT];
-            bool valid[RPT], isp[RPT];
-            u64 wv[RPT], o0[RPT], o1[RPT];
-            // (a) rows of this pass: position -> physical row
-#pragma unroll
-            for (int j = 0; j < RPT; ++j) {
-                const int p = pb + j * RPP + rg;
-                valid[j] = p < p_end;
-                isp[j] = valid[j] && p < r + kbar;
-                ph[j] = !valid[j] ? 0 : (isp[j] ? st->prow[p - r] : trailing_row(perm, st, r, nwin, nx, p));
-            }
-            // (b) their panel words and current words of the tile, all in flight
-#pragma unroll
-            for (int j = 0; j < RPT; ++j) {
-                const bool live = valid[j] && !isp[j];
-                wv[j] = live ? side_cur[ph[j]] : 0ull;
-                o0[j] = 0;
-                o1[j] = 0;
-                if (live && wact) {
-                    const uint64_t *a = A + (int64_t)ph[j] * stride + w0;
-                    if (two) {
-                        const ulonglong2 v2 = *reinterpret_cast<const ulonglong2 *>(a);
-                        o0[j] = v2.x;
-                        o1[j] = v2.y;
-                    } else {
-                        o0[j] = a[0];
-                    }
-                }
-            }
+            pass_rows<RPT, RPP>(pb + 2 * PASS, rg, p_end, r, kbar, nwin, nx, st, perm, phC, validC, ispC);
+            pass_loads<RPT>(A, stride, side_cur, w0, two, wact, phB, validB, ispB, wvB, o0B, o1B);
             // (c) coordinates, table lookups, stores
 #pragma unroll
             for (int j = 0; j < RPT; ++j) {
@@ -1019,6 +1042,18 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
                     else if (two && w0 + 1 == b + 1)
                         side_nxt[ph[j]] = n1;
                 }
+            }
+#pragma unroll
+            for (int j = 0; j < RPT; ++j) {
+                ph[j] = phB[j];
+                valid[j] = validB[j];
+                isp[j] = ispB[j];
+                wv[j] = wvB[j];
+                o0[j] = o0B[j];
+                o1[j] = o1B[j];
+                phB[j] = phC[j];
+                validB[j] = validC[j];
+                ispB[j] = ispC[j];
             }
         }
     }
@@ -1232,8 +1267,8 @@ __global__ void __launch_bounds__(PIVOT_THREADS, 1) k_pivot_b(const gf2::ElimDes
                 d.P, d.Q, d.m, b, nbits);
 }
 
-template <int TW, int RPT, int MINB>
-__global__ void __launch_bounds__(256, MINB)
+template <int TW, int RPT, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
 k_sweep_b(const gf2::ElimDesc *__restrict__ D, const int *__restrict__ idx, const int *__restrict__ pre, int nact, int b)
 {
     // matrix j with pre[j] <= blockIdx.x < pre[j + 1]
@@ -1246,7 +1281,7 @@ k_sweep_b(const gf2::ElimDesc *__restrict__ D, const int *__restrict__ idx, cons
             hi = mid - 1;
     }
     const gf2::ElimDesc &d = D[idx[lo]];
-    sweep_panel<TW, RPT, 256>(d.A, d.stride, d.side + (size_t)(b & 1) * d.m, d.side + (size_t)((b + 1) & 1) * d.m,
+    sweep_panel<TW, RPT, NT>(d.A, d.stride, d.side + (size_t)(b & 1) * d.m, d.side + (size_t)((b + 1) & 1) * d.m,
                               d.perm, d.st + (b & 1), d.out, d.ostride, d.m, d.W, b, (int)blockIdx.x - pre[lo],
                               pre[lo + 1] - pre[lo]);
 }
@@ -1296,7 +1331,8 @@ __global__ void k_copyback_b(const gf2::ElimDesc *__restrict__ D)
 
 namespace gf2 {
 
-int sweep_rows_per_pass(int tile_words) { return tile_words == 4 ? (256 / 2) * 4 : (256 / 4) * 4; }
+// rows per pass of the batched sweep variants below (threads / threads per row)
+int sweep_rows_per_pass(int tile_words) { return tile_words == 4 ? 512 / 2 : 1024 / 4; }
 int sweep_ctas_per_sm(int tile_words) { return tile_words == 4 ? 2 : 1; }
 
 int batch_init(const ElimDesc *D, int count, int max_m, cudaStream_t s)
@@ -1320,7 +1356,7 @@ int batch_pivot(const ElimDesc *D, const int *idx, int nact, int b, cudaStream_t
     return note_cuda(cudaGetLastError());
 }
 
-template <int TW, int RPT, int MINB>
+template <int TW, int RPT, int NT, int MINB>
 static int launch_sweep_b(const ElimDesc *D, const int *idx, const int *pre, int nact, int total, int b,
                           cudaStream_t s)
 {
@@ -1328,13 +1364,13 @@ static int launch_sweep_b(const ElimDesc *D, const int *idx, const int *pre, int
     constexpr size_t smem = sweep_smem<TW>();
     if (!attr_set) {
         cudaError_t err =
-            cudaFuncSetAttribute(k_sweep_b<TW, RPT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_sweep_b<TW, RPT, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess)
             return note_cuda(err);
         attr_set = true;
     }
     const int tok = prof_begin(s);
-    k_sweep_b<TW, RPT, MINB><<<total, 256, smem, s>>>(D, idx, pre, nact, b);
+    k_sweep_b<TW, RPT, NT, MINB><<<total, NT, smem, s>>>(D, idx, pre, nact, b);
     prof_end(s, GF2_PROF_SWEEP, tok);
     prof_launched(1);
     return note_cuda(cudaGetLastError());
@@ -1345,8 +1381,8 @@ int batch_sweep(const ElimDesc *D, const int *idx, const int *pre, int nact, int
 {
     if (nact <= 0 || total <= 0)
         return GF2_OK;
-    return tile_words == 4 ? launch_sweep_b<4, 4, 2>(D, idx, pre, nact, total, b, s)
-                           : launch_sweep_b<8, 4, 1>(D, idx, pre, nact, total, b, s);
+    return tile_words == 4 ? launch_sweep_b<4, 1, 512, 2>(D, idx, pre, nact, total, b, s)
+                           : launch_sweep_b<8, 1, 1024, 1>(D, idx, pre, nact, total, b, s);
 }
 
 int batch_finish(const ElimDesc *D, int count, int max_m, cudaStream_t s)
@@ -1456,7 +1492,7 @@ int elim_run(const Elim &e)
         if ((rc = note_cuda(cudaGetLastError())) || (rc = note_cuda(cudaEventRecord(ev_piv, e.s))) ||
             (rc = note_cuda(cudaStreamWaitEvent(t, ev_piv, 0))))
             return rc;
-        rc = e.tile_words == 4   ? launch_sweep<4, 4, 256, 2>(e, b, t)
+        rc = e.tile_words == 4   ? launch_sweep<4, 1, 512, 2>(e, b, t)
              : e.tile_words == 8 ? launch_sweep<8, 1, 1024, 1>(e, b, t)
                                  : launch_sweep<16, 1, 1024, 1>(e, b, t);
         if (rc || (rc = note_cuda(cudaEventRecord(ev_rest[b & 1], t))))
