@@ -96,107 +96,163 @@ __global__ void k_diag_inv(const uint64_t *__restrict__ U1, int64_t stride, cons
     Dinv[(int64_t)q * 64 + lane + 32] = x1;
 }
 
-// Gray-code tables of 64 rows x TWB words: T[g][v][w] = sum of rows 8g+e (bit e of v).
-template <int TWB>
-__device__ __forceinline__ void build_tables(const u64 *__restrict__ rows, u64 *__restrict__ T, int tid)
+// Back substitution X = U1^-1 B over groups of G blocks of 64 pivots, from the
+// last group up. Within a group (k_rref_group, one CTA per tile of TW1 words of
+// B): for each block q from the group's last to its first,
+//   X_q = Dinv_q . B_q              (B_q holds every update from below),
+//   B_i += U1[i, block q] . X_q     for the group's rows i above block q.
+// Then (k_rref_bulk) every row above the group takes the whole group at once:
+//   B_i += sum over the group's blocks q of U1[i, block q] . X_q,
+// with one Gray-code table per 8 pivots (G x 8 tables).
+constexpr int G = 8;     // blocks per group
+constexpr int TW1 = 2;   // words of B per CTA in the group solve
+constexpr int TWG = 1;   // words of B per CTA in the bulk update
+static_assert(TWG == 1, "the bulk update's lookups assume one word per tile");
+
+__global__ void __launch_bounds__(256, 1)
+k_rref_group(u64 *__restrict__ Bc, u64 *__restrict__ Xc, int64_t sb, const uint64_t *__restrict__ U1,
+             int64_t stride, const u64 *__restrict__ Dinv, const PanelState *__restrict__ st, int n, int q0)
 {
-    for (int e = tid; e < 8 * TWB * 16; e += blockDim.x) {
-        const int vh = e & 15, gw = e >> 4, wi = gw % TWB, g = gw / TWB;
-        const u64 *Og = rows + (8 * g) * TWB + wi;
-        u64 cur = 0;
+    extern __shared__ __align__(16) u64 smg[];
+    u64 *sB = smg;                   // [G * 64][TW1]  the group's rows of B
+    u64 *sU = sB + G * 64 * TW1;     // [G * 64][G]    the group's rows of U1 at the group's blocks
+    u64 *sT = sU + G * 64 * G;       // [8][256][TW1]  tables of X_q
+    u64 *sX = sT + 8 * 256 * TW1;    // [64][TW1]
+    u64 *sD = sX + 64 * TW1;         // [64]
+    const int r = st->r_next;
+    const int NB = (n - r + 63) >> 6;
+    const int base = 64 * q0;
+    if (base >= r || NB == 0)
+        return;
+    const int tid = threadIdx.x;
+    const int wb = blockIdx.x * TW1;
+    if (wb >= NB)
+        return;
+    const int rows = min(G * 64, r - base);
+    const int qend = q0 + (rows + 63) / 64;  // one past the group's last block
+    for (int e = tid; e < G * 64 * TW1; e += blockDim.x) {
+        const int i = e / TW1, w = e % TW1;
+        sB[e] = (i < rows && wb + w < NB) ? Bc[(int64_t)(base + i) * sb + wb + w] : 0ull;
+    }
+    for (int e = tid; e < G * 64 * G; e += blockDim.x) {
+        const int i = e / G, qq = e % G;
+        sU[e] = (i < rows && q0 + qq < qend) ? U1[(int64_t)(base + i) * stride + q0 + qq] : 0ull;
+    }
+    for (int q = qend - 1; q >= q0; --q) {
+        const int lq = q - q0;
+        const int nrow = min(64, r - 64 * q);
+        __syncthreads();
+        if (tid < 64)
+            sD[tid] = Dinv[(int64_t)q * 64 + tid];
+        __syncthreads();
+        // X_q = Dinv_q B_q
+        for (int e = tid; e < 64 * TW1; e += blockDim.x) {
+            const int s2 = e / TW1, w = e % TW1;
+            u64 d = sD[s2], x = 0;
+            while (d) {
+                const int k = ctz64(d);
+                d &= d - 1;
+                x ^= sB[(lq * 64 + k) * TW1 + w];
+            }
+            sX[e] = x;
+            if (s2 < nrow && wb + w < NB)
+                Xc[(int64_t)(64 * q + s2) * sb + wb + w] = x;
+        }
+        if (lq == 0)
+            break;  // no group rows above the first block
+        __syncthreads();
+        // Gray-code tables of X_q's rows
+        for (int e = tid; e < 8 * TW1 * 16; e += blockDim.x) {
+            const int w = e % TW1, rest = e / TW1, vh = rest & 15, g = rest >> 4;
+            const u64 *Xg = sX + (8 * g) * TW1 + w;
+            u64 cur = 0;
 #pragma unroll
-        for (int bit = 0; bit < 4; ++bit)
-            if ((vh >> bit) & 1)
-                cur ^= Og[(4 + bit) * TWB];
-        u64 *Tg = T + (g * 256 + (vh << 4)) * TWB + wi;
-        Tg[0] = cur;
+            for (int bit = 0; bit < 4; ++bit)
+                if ((vh >> bit) & 1)
+                    cur ^= Xg[(4 + bit) * TW1];
+            u64 *Tg = sT + (g * 256 + (vh << 4)) * TW1 + w;
+            Tg[0] = cur;
 #pragma unroll
-        for (int i = 1; i < 16; ++i) {
-            cur ^= Og[(__ffs(i) - 1) * TWB];
-            Tg[(i ^ (i >> 1)) * TWB] = cur;
+            for (int i = 1; i < 16; ++i) {
+                cur ^= Xg[(__ffs(i) - 1) * TW1];
+                Tg[(i ^ (i >> 1)) * TW1] = cur;
+            }
+        }
+        __syncthreads();
+        // the group's rows above block q
+        for (int e = tid; e < lq * 64 * TW1; e += blockDim.x) {
+            const int i = e / TW1, w = e % TW1;
+            const u64 u = sU[i * G + lq];
+            u64 acc = 0;
+#pragma unroll
+            for (int g = 0; g < 8; ++g)
+                acc ^= sT[(g * 256 + (int)((u >> (8 * g)) & 255ull)) * TW1 + w];
+            sB[e] ^= acc;
         }
     }
 }
 
-// One 64-pivot block q of the back substitution X = U1^-1 B:
-//   X_q = Dinv_q . B_q            (B_q already holds every update from below)
-//   B_i += U1[i, block q] . X_q   for every row i above the block.
-constexpr int TWB = 2;
 __global__ void __launch_bounds__(256, 1)
-k_rref_step(u64 *__restrict__ Bc, u64 *__restrict__ Xc, int64_t sb, const uint64_t *__restrict__ U1,
-            int64_t stride, const u64 *__restrict__ Dinv, const PanelState *__restrict__ st, int n, int q)
+k_rref_bulk(u64 *__restrict__ Bc, const u64 *__restrict__ Xc, int64_t sb, const uint64_t *__restrict__ U1,
+            int64_t stride, const PanelState *__restrict__ st, int n, int q0)
 {
-    extern __shared__ __align__(16) u64 smr[];
-    u64 *sTB = smr;                  // [8][256][TWB]
-    u64 *sTX = sTB + 8 * 256 * TWB;  // [8][256][TWB]
-    u64 *sB = sTX + 8 * 256 * TWB;   // [64][TWB]
-    u64 *sX = sB + 64 * TWB;         // [64][TWB]
-    u64 *sD = sX + 64 * TWB;         // [64]
+    extern __shared__ __align__(16) u64 smk[];
+    u64 *sT = smk;                      // [G][8][256][TWG]
+    u64 *sXg = sT + G * 8 * 256 * TWG;  // [G * 64][TWG]
     const int r = st->r_next;
-    const int nn = n - r;
-    const int NB = (nn + 63) >> 6;
-    const int base = 64 * q;
-    if (base >= r || NB == 0)
+    const int NB = (n - r + 63) >> 6;
+    const int above = 64 * q0;
+    if (above == 0 || above >= r || NB == 0)
         return;
     const int tid = threadIdx.x;
-    const int nrow = min(64, r - base);
-    const int tiles = (NB + TWB - 1) / TWB;
-    const int above = base;
+    const int nblk = min(G, (r - above + 63) / 64);
+    const int tiles = (NB + TWG - 1) / TWG;
     int chunks = gridDim.x / tiles;
     if (chunks < 1)
         chunks = 1;
-    int R = (above + chunks - 1) / chunks;
-    R = (R + 255) / 256 * 256;
-    if (R == 0)
-        R = 256;
-    chunks = above > 0 ? (above + R - 1) / R : 1;
+    const int R = (above + chunks - 1) / chunks;
     const int items = tiles * chunks;
-    if (tid < 64)
-        sD[tid] = Dinv[(int64_t)q * 64 + tid];
     int cur_tile = -1;
     for (int item = blockIdx.x; item < items; item += gridDim.x) {
         const int tile = item / chunks, chunk = item % chunks;
-        const int wb = tile * TWB;
+        const int wb = tile * TWG;
         if (tile != cur_tile) {
             __syncthreads();
-            for (int e = tid; e < 64 * TWB; e += blockDim.x) {
-                const int s = e / TWB, wi = e % TWB;
-                sB[e] = (s < nrow && wb + wi < NB) ? Bc[(int64_t)(base + s) * sb + wb + wi] : 0ull;
+            for (int e = tid; e < G * 64 * TWG; e += blockDim.x) {
+                const int i = e / TWG, w = e % TWG;
+                sXg[e] = (i < min(G * 64, r - above) && wb + w < NB) ? Xc[(int64_t)(above + i) * sb + wb + w] : 0ull;
             }
             __syncthreads();
-            build_tables<TWB>(sB, sTB, tid);
-            __syncthreads();
-            for (int e = tid; e < 64 * TWB; e += blockDim.x) {
-                const int s = e / TWB, wi = e % TWB;
-                const u64 d = sD[s];
-                u64 acc = 0;
+            for (int e = tid; e < nblk * 8 * TWG * 16; e += blockDim.x) {
+                const int w = e % TWG, rest = e / TWG, vh = rest & 15, g = (rest >> 4) & 7, qq = rest >> 7;
+                const u64 *Xg = sXg + (64 * qq + 8 * g) * TWG + w;
+                u64 cur = 0;
 #pragma unroll
-                for (int g = 0; g < 8; ++g)
-                    acc ^= sTB[(g * 256 + (int)((d >> (8 * g)) & 255ull)) * TWB + wi];
-                sX[e] = acc;
-                if (chunk == 0 && s < nrow && wb + wi < NB)
-                    Xc[(int64_t)(base + s) * sb + wb + wi] = acc;
+                for (int bit = 0; bit < 4; ++bit)
+                    if ((vh >> bit) & 1)
+                        cur ^= Xg[(4 + bit) * TWG];
+                u64 *Tg = sT + ((qq * 8 + g) * 256 + (vh << 4)) * TWG + w;
+                Tg[0] = cur;
+#pragma unroll
+                for (int i = 1; i < 16; ++i) {
+                    cur ^= Xg[(__ffs(i) - 1) * TWG];
+                    Tg[(i ^ (i >> 1)) * TWG] = cur;
+                }
             }
-            __syncthreads();
-            build_tables<TWB>(sX, sTX, tid);
             __syncthreads();
             cur_tile = tile;
         }
         const int i0 = chunk * R, i1 = min(above, i0 + R);
         for (int i = i0 + tid; i < i1; i += blockDim.x) {
-            const u64 u = U1[(int64_t)i * stride + q];
-            u64 a0 = 0, a1 = 0;
+            const uint64_t *urow = U1 + (int64_t)i * stride + q0;
+            u64 acc = 0;
+            for (int qq = 0; qq < nblk; ++qq) {
+                const u64 u = urow[qq];
 #pragma unroll
-            for (int g = 0; g < 8; ++g) {
-                const ulonglong2 e2 =
-                    *reinterpret_cast<const ulonglong2 *>(sTX + (g * 256 + (int)((u >> (8 * g)) & 255ull)) * TWB);
-                a0 ^= e2.x;
-                a1 ^= e2.y;
+                for (int g = 0; g < 8; ++g)
+                    acc ^= sT[((qq * 8 + g) * 256 + (int)((u >> (8 * g)) & 255ull)) * TWG];
             }
-            u64 *brow = Bc + (int64_t)i * sb + wb;
-            brow[0] ^= a0;
-            if (wb + 1 < NB)
-                brow[1] ^= a1;
+            Bc[(int64_t)i * sb + wb] ^= acc;
         }
     }
 }
@@ -284,19 +340,30 @@ int rref_finish(const Elim &e, const ElimLayout &L, char *work, int64_t *rank, i
     if (rc)
         return rc;
     const int grid = sm_count();
-    const size_t smem = (size_t)(2 * 8 * 256 * TWB + 2 * 64 * TWB + 64) * sizeof(u64);
+    const size_t smem_g = (size_t)(G * 64 * TW1 + G * 64 * G + 8 * 256 * TW1 + 64 * TW1 + 64) * sizeof(u64);
+    const size_t smem_b = (size_t)(G * 8 * 256 * TWG + G * 64 * TWG) * sizeof(u64);
     static bool attr_set = false;
     if (!attr_set) {
-        rc = note_cuda(cudaFuncSetAttribute(k_rref_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        rc = note_cuda(cudaFuncSetAttribute(k_rref_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g));
+        if (!rc)
+            rc = note_cuda(
+                cudaFuncSetAttribute(k_rref_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
         if (rc)
             return rc;
         attr_set = true;
     }
-    for (int q = nblk - 1; q >= 0; --q) {
-        const int tok = prof_begin(e.s);
-        k_rref_step<<<grid, 256, smem, e.s>>>(Bc, Xc, sb, e.A, e.stride, Dinv, e.stf, n, q);
+    // B tiles of the group solve: ceil(NB / TW1) CTAs, NB <= W
+    const int gtiles = (W + TW1 - 1) / TW1;
+    for (int q0 = (nblk - 1) / G * G; q0 >= 0; q0 -= G) {
+        int tok = prof_begin(e.s);
+        k_rref_group<<<gtiles, 256, smem_g, e.s>>>(Bc, Xc, sb, e.A, e.stride, Dinv, e.stf, n, q0);
         prof_end(e.s, GF2_PROF_RREF, tok);
-        prof_launched(1);
+        if (q0 > 0) {
+            tok = prof_begin(e.s);
+            k_rref_bulk<<<grid, 256, smem_b, e.s>>>(Bc, Xc, sb, e.A, e.stride, e.stf, n, q0);
+            prof_end(e.s, GF2_PROF_RREF, tok);
+        }
+        prof_launched(q0 > 0 ? 2 : 1);
         rc = note_cuda(cudaGetLastError());
         if (rc)
             return rc;
