@@ -85,6 +85,22 @@ __device__ __forceinline__ u64 pdep64(u64 x, u64 m)
     return r;
 }
 
+// MakeTable's Gray-code enumeration (Sec. 3.1) of the 16 sums base + {subsets
+// of rows r0..r3}: entry gray(i) is entry gray(i - 1) plus one row, stored at
+// T[gray(i) * ts]. The four rows come in registers, so the chain of stores
+// never waits on a load that might alias them.
+__device__ __forceinline__ void gray16(u64 base, u64 r0, u64 r1, u64 r2, u64 r3, u64 *__restrict__ T, int ts)
+{
+    u64 cur = base;
+    T[0] = cur;
+#pragma unroll
+    for (int i = 1; i < 16; ++i) {
+        const int k = __ffs(i) - 1;  // the row that changes between gray(i - 1) and gray(i)
+        cur ^= k == 0 ? r0 : k == 1 ? r1 : k == 2 ? r2 : r3;
+        T[(i ^ (i >> 1)) * ts] = cur;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // bounded waits and the device status word
 // ---------------------------------------------------------------------------

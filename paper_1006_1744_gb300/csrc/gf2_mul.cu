@@ -50,20 +50,14 @@ k_mul_xor(uint64_t *__restrict__ C, int64_t sc, const uint64_t *__restrict__ A, 
             const int kk = min(64, k - 64 * q);
             const int ng = (kk + 7) >> 3;
             for (int e = tid; e < ng * TW * 16; e += 256) {
-                const int vh = e & 15, gw = e >> 4, wi = gw % TW, g = gw / TW;
+                const int wi = e % TW, rest = e / TW, vh = rest & 15, g = rest >> 4;
                 const u64 *Og = sO + (8 * g) * TW + wi;
                 u64 cur = 0;
 #pragma unroll
                 for (int bit = 0; bit < 4; ++bit)
                     if ((vh >> bit) & 1)
                         cur ^= Og[(4 + bit) * TW];
-                u64 *Tg = sT + (g * 256 + (vh << 4)) * TW + wi;
-                Tg[0] = cur;
-#pragma unroll
-                for (int i = 1; i < 16; ++i) {
-                    cur ^= Og[(__ffs(i) - 1) * TW];
-                    Tg[(i ^ (i >> 1)) * TW] = cur;
-                }
+                gray16(cur, Og[0], Og[TW], Og[2 * TW], Og[3 * TW], sT + (g * 256 + (vh << 4)) * TW + wi, TW);
             }
             __syncthreads();
             u64 cur_a[RPT];

@@ -909,13 +909,7 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
                 for (int bit = 0; bit < HIB; ++bit)
                     if ((vh >> bit) & 1)
                         cur ^= Og[(4 + bit) * TW];
-                u64 *Tg = sT + (g * TE + (vh << 4)) * TW + wi;
-                Tg[0] = cur;
-#pragma unroll
-                for (int i = 1; i < 16; ++i) {
-                    cur ^= Og[(__ffs(i) - 1) * TW];
-                    Tg[(i ^ (i >> 1)) * TW] = cur;
-                }
+                gray16(cur, Og[0], Og[TW], Og[2 * TW], Og[3 * TW], sT + (g * TE + (vh << 4)) * TW + wi, TW);
             }
             if (HALF)
                 for (int e = tid; e < TW * 16; e += NT) {
@@ -926,13 +920,7 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
                     for (int bit = 0; bit < 4; ++bit)
                         if ((vh >> bit) & 1)
                             cur ^= O7[8 * (4 + bit) * TW];
-                    u64 *Ug = sU + (vh << 4) * TW + wi;
-                    Ug[0] = cur;
-#pragma unroll
-                    for (int i = 1; i < 16; ++i) {
-                        cur ^= O7[8 * (__ffs(i) - 1) * TW];
-                        Ug[(i ^ (i >> 1)) * TW] = cur;
-                    }
+                    gray16(cur, O7[0], O7[8 * TW], O7[16 * TW], O7[24 * TW], sU + (vh << 4) * TW + wi, TW);
                 }
             __syncthreads();
             cur_tile = tile;

@@ -161,20 +161,14 @@ template <int TWB>
 __device__ __forceinline__ void rec_tables(const u64 *__restrict__ rows, u64 *__restrict__ T, int tid)
 {
     for (int e = tid; e < 8 * TWB * 16; e += blockDim.x) {
-        const int vh = e & 15, gw = e >> 4, wi = gw % TWB, g = gw / TWB;
+        const int wi = e % TWB, rest = e / TWB, vh = rest & 15, g = rest >> 4;
         const u64 *Og = rows + (8 * g) * TWB + wi;
         u64 cur = 0;
 #pragma unroll
         for (int bit = 0; bit < 4; ++bit)
             if ((vh >> bit) & 1)
                 cur ^= Og[(4 + bit) * TWB];
-        u64 *Tg = T + (g * 256 + (vh << 4)) * TWB + wi;
-        Tg[0] = cur;
-#pragma unroll
-        for (int i = 1; i < 16; ++i) {
-            cur ^= Og[(__ffs(i) - 1) * TWB];
-            Tg[(i ^ (i >> 1)) * TWB] = cur;
-        }
+        gray16(cur, Og[0], Og[TWB], Og[2 * TWB], Og[3 * TWB], T + (g * 256 + (vh << 4)) * TWB + wi, TWB);
     }
 }
 

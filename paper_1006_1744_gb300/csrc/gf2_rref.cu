@@ -109,6 +109,23 @@ constexpr int TW1 = 2;   // words of B per CTA in the group solve
 constexpr int TWG = 1;   // words of B per CTA in the bulk update
 static_assert(TWG == 1, "the bulk update's lookups assume one word per tile");
 
+// Gray-code tables of 64 rows x TW words: T[g][v][w] = sum of the rows 8 g + e
+// for the set bits e of v (MakeTable: each entry one row away from the last)
+template <int TW>
+__device__ __forceinline__ void gray_tables(const u64 *__restrict__ rows, u64 *__restrict__ T, int tid)
+{
+    for (int e = tid; e < 8 * TW * 16; e += blockDim.x) {
+        const int w = e % TW, rest = e / TW, vh = rest & 15, g = rest >> 4;
+        const u64 *Og = rows + (8 * g) * TW + w;
+        u64 cur = 0;
+#pragma unroll
+        for (int bit = 0; bit < 4; ++bit)
+            if ((vh >> bit) & 1)
+                cur ^= Og[(4 + bit) * TW];
+        gray16(cur, Og[0], Og[TW], Og[2 * TW], Og[3 * TW], T + (g * 256 + (vh << 4)) * TW + w, TW);
+    }
+}
+
 __global__ void __launch_bounds__(256, 1)
 k_rref_group(u64 *__restrict__ Bc, u64 *__restrict__ Xc, int64_t sb, const uint64_t *__restrict__ U1,
              int64_t stride, const u64 *__restrict__ Dinv, const PanelState *__restrict__ st, int n, int q0)
@@ -118,7 +135,7 @@ k_rref_group(u64 *__restrict__ Bc, u64 *__restrict__ Xc, int64_t sb, const uint6
     u64 *sU = sB + G * 64 * TW1;     // [G * 64][G]    the group's rows of U1 at the group's blocks
     u64 *sT = sU + G * 64 * G;       // [8][256][TW1]  tables of X_q
     u64 *sX = sT + 8 * 256 * TW1;    // [64][TW1]
-    u64 *sD = sX + 64 * TW1;         // [64]
+    u64 *sD = sX + 64 * TW1;         // [G][64] inverses of the group's diagonal blocks
     const int r = st->r_next;
     const int NB = (n - r + 63) >> 6;
     const int base = 64 * q0;
@@ -138,22 +155,22 @@ k_rref_group(u64 *__restrict__ Bc, u64 *__restrict__ Xc, int64_t sb, const uint6
         const int i = e / G, qq = e % G;
         sU[e] = (i < rows && q0 + qq < qend) ? U1[(int64_t)(base + i) * stride + q0 + qq] : 0ull;
     }
+    for (int e = tid; e < (qend - q0) * 64; e += blockDim.x)
+        sD[e] = Dinv[(int64_t)q0 * 64 + e];
     for (int q = qend - 1; q >= q0; --q) {
         const int lq = q - q0;
         const int nrow = min(64, r - 64 * q);
         __syncthreads();
-        if (tid < 64)
-            sD[tid] = Dinv[(int64_t)q * 64 + tid];
+        // X_q = Dinv_q B_q: tables of B_q's rows, eight lookups per row of X_q
+        gray_tables<TW1>(sB + lq * 64 * TW1, sT, tid);
         __syncthreads();
-        // X_q = Dinv_q B_q
         for (int e = tid; e < 64 * TW1; e += blockDim.x) {
             const int s2 = e / TW1, w = e % TW1;
-            u64 d = sD[s2], x = 0;
-            while (d) {
-                const int k = ctz64(d);
-                d &= d - 1;
-                x ^= sB[(lq * 64 + k) * TW1 + w];
-            }
+            const u64 d = sD[lq * 64 + s2];
+            u64 x = 0;
+#pragma unroll
+            for (int g = 0; g < 8; ++g)
+                x ^= sT[(g * 256 + (int)((d >> (8 * g)) & 255ull)) * TW1 + w];
             sX[e] = x;
             if (s2 < nrow && wb + w < NB)
                 Xc[(int64_t)(64 * q + s2) * sb + wb + w] = x;
@@ -161,23 +178,7 @@ k_rref_group(u64 *__restrict__ Bc, u64 *__restrict__ Xc, int64_t sb, const uint6
         if (lq == 0)
             break;  // no group rows above the first block
         __syncthreads();
-        // Gray-code tables of X_q's rows
-        for (int e = tid; e < 8 * TW1 * 16; e += blockDim.x) {
-            const int w = e % TW1, rest = e / TW1, vh = rest & 15, g = rest >> 4;
-            const u64 *Xg = sX + (8 * g) * TW1 + w;
-            u64 cur = 0;
-#pragma unroll
-            for (int bit = 0; bit < 4; ++bit)
-                if ((vh >> bit) & 1)
-                    cur ^= Xg[(4 + bit) * TW1];
-            u64 *Tg = sT + (g * 256 + (vh << 4)) * TW1 + w;
-            Tg[0] = cur;
-#pragma unroll
-            for (int i = 1; i < 16; ++i) {
-                cur ^= Xg[(__ffs(i) - 1) * TW1];
-                Tg[(i ^ (i >> 1)) * TW1] = cur;
-            }
-        }
+        gray_tables<TW1>(sX, sT, tid);  // tables of X_q's rows
         __syncthreads();
         // the group's rows above block q
         for (int e = tid; e < lq * 64 * TW1; e += blockDim.x) {
@@ -216,6 +217,12 @@ k_rref_bulk(u64 *__restrict__ Bc, const u64 *__restrict__ Xc, int64_t sb, const 
     for (int item = blockIdx.x; item < items; item += gridDim.x) {
         const int tile = item / chunks, chunk = item % chunks;
         const int wb = tile * TWG;
+        const int i0 = chunk * R, i1 = min(above, i0 + R);
+        // this thread's first row of U1, in flight while the tables are built
+        u64 upre[G];
+#pragma unroll
+        for (int qq = 0; qq < G; ++qq)
+            upre[qq] = (i0 + tid < i1 && qq < nblk) ? U1[(int64_t)(i0 + tid) * stride + q0 + qq] : 0ull;
         if (tile != cur_tile) {
             __syncthreads();
             for (int e = tid; e < G * 64 * TWG; e += blockDim.x) {
@@ -231,26 +238,23 @@ k_rref_bulk(u64 *__restrict__ Bc, const u64 *__restrict__ Xc, int64_t sb, const 
                 for (int bit = 0; bit < 4; ++bit)
                     if ((vh >> bit) & 1)
                         cur ^= Xg[(4 + bit) * TWG];
-                u64 *Tg = sT + ((qq * 8 + g) * 256 + (vh << 4)) * TWG + w;
-                Tg[0] = cur;
-#pragma unroll
-                for (int i = 1; i < 16; ++i) {
-                    cur ^= Xg[(__ffs(i) - 1) * TWG];
-                    Tg[(i ^ (i >> 1)) * TWG] = cur;
-                }
+                gray16(cur, Xg[0], Xg[TWG], Xg[2 * TWG], Xg[3 * TWG], sT + ((qq * 8 + g) * 256 + (vh << 4)) * TWG + w,
+                       TWG);
             }
             __syncthreads();
             cur_tile = tile;
         }
-        const int i0 = chunk * R, i1 = min(above, i0 + R);
         for (int i = i0 + tid; i < i1; i += blockDim.x) {
             const uint64_t *urow = U1 + (int64_t)i * stride + q0;
             u64 acc = 0;
-            for (int qq = 0; qq < nblk; ++qq) {
-                const u64 u = urow[qq];
 #pragma unroll
-                for (int g = 0; g < 8; ++g)
-                    acc ^= sT[((qq * 8 + g) * 256 + (int)((u >> (8 * g)) & 255ull)) * TWG];
+            for (int qq = 0; qq < G; ++qq) {
+                if (qq < nblk) {
+                    const u64 u = i == i0 + tid ? upre[qq] : urow[qq];
+#pragma unroll
+                    for (int g = 0; g < 8; ++g)
+                        acc ^= sT[((qq * 8 + g) * 256 + (int)((u >> (8 * g)) & 255ull)) * TWG];
+                }
             }
             Bc[(int64_t)i * sb + wb] ^= acc;
         }
@@ -340,7 +344,7 @@ int rref_finish(const Elim &e, const ElimLayout &L, char *work, int64_t *rank, i
     if (rc)
         return rc;
     const int grid = sm_count();
-    const size_t smem_g = (size_t)(G * 64 * TW1 + G * 64 * G + 8 * 256 * TW1 + 64 * TW1 + 64) * sizeof(u64);
+    const size_t smem_g = (size_t)(G * 64 * TW1 + G * 64 * G + 8 * 256 * TW1 + 64 * TW1 + G * 64) * sizeof(u64);
     const size_t smem_b = (size_t)(G * 8 * 256 * TWG + G * 64 * TWG) * sizeof(u64);
     static bool attr_set = false;
     if (!attr_set) {
