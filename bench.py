@@ -131,7 +131,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     n = args.n
-    ns = min(n, 8192)  # bounded sample per step; time scaled by (n/ns)^3 (cubic elimination)
+    ns = min(n, 4096)  # bounded sample per step; time scaled by (n/ns)^3 (cubic elimination)
     scale = (n / ns) ** 3
     for _ in range(args.warmup):
         cpu_oracle_sample(ns)
@@ -152,20 +152,219 @@ def run_reference(args):
     return 0
 
 
+def max_over_ranks(value: float, world: int, device="cpu") -> float:
+    """The slowest rank's value (every rank gets it); the identity for one process."""
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_seconds_per_matrix(step_ms_max: float, world: int) -> float:
+    """Replicas: every rank eliminates its own matrix per step, so the job finishes
+    world matrices per (slowest) step."""
+    return step_ms_max / 1e3 / world
+
+
+def _timed(fn, steps, warmup, pre=None):
+    """CUDA-event time of fn() (ms), mean over steps after warmup; pre() runs untimed before each."""
+    import torch
+    for _ in range(warmup):
+        if pre:
+            pre()
+        fn()
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        if pre:
+            pre()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / steps
+
+
+def _freivalds(A, B, C, m, k, n, trials=2, seed=1):
+    """CPU check that A = B.C over GF(2): A.x == B.(C.x) for random bit vectors x."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    pc = np.array([bin(i).count("1") & 1 for i in range(256)], dtype=np.uint8)
+
+    def matvec(M, rows, cols, x):
+        W = (cols + 63) // 64
+        t = (M[:rows, :W] & x[None, :W]).view(np.uint8).reshape(rows, -1)
+        return np.bitwise_xor.reduce(pc[t], axis=1).astype(np.uint8)
+
+    def pack(bits, stride_words):
+        out = np.zeros(stride_words * 64, dtype=np.uint8)
+        out[:bits.size] = bits
+        return np.packbits(out, bitorder="little").view(np.uint64)
+
+    for _ in range(trials):
+        xb = rng.integers(0, 2, n, dtype=np.uint8)
+        x = pack(xb, C.shape[1])
+        cx = matvec(C, k, n, x)
+        lhs = matvec(A, m, n, x)
+        rhs = matvec(B, m, k, pack(cx, B.shape[1]))
+        if not np.array_equal(lhs, rhs):
+            return False
+    return True
+
+
+def _base_line(args, value, unit, ms, config, clocks, launches, extra):
+    line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": config, "clocks": clocks, "gpu_launches": launches}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_config3(args):
+    """65536 x 65536 matrices (512 MB packed): dense Bernoulli(1/2), A = B.C with B 65536 x 32768 and
+    C 32768 x 65536 (rank <= 32768), and Bernoulli(0.01); each through the panel elimination alone
+    (MMPF) and the recursive PLS with the XOR-table and the tensor-core trailing product."""
+    import torch
+    from paper_1006_1744_gb300 import build, gf2, synth, synth_gpu
+    build.build()
+    n = 65536
+    k = 32768
+    st = synth.default_stride(n)
+    dev = torch.device("cuda", 0)
+    A0 = torch.empty((n, st), dtype=torch.int64, device=dev)
+    A = torch.empty_like(A0)
+    methods = {"mmpf": None, "rec_xor": {"cutoff_cols": 4096, "product": 1},
+               "rec_tc": {"cutoff_cols": 4096, "product": 2}}
+    steps = max(1, min(args.steps, 3))
+    results = {}
+    checks = {}
+    sampler = ClockSampler(0)
+    sampler.start()
+    gf2.prof_reset()
+    gf2.prof_enable(1)
+    for variant in ("dense", "product", "sparse01"):
+        if variant == "dense":
+            synth_gpu.fill(A0, n, SEED)
+        elif variant == "sparse01":
+            synth_gpu.fill(A0, n, SEED + 2, p=0.01)
+        else:
+            B = torch.empty((n, synth.default_stride(k)), dtype=torch.int64, device=dev)
+            C = torch.empty((k, st), dtype=torch.int64, device=dev)
+            synth_gpu.fill(B, k, SEED + 3)
+            synth_gpu.fill(C, n, SEED + 4)
+            gf2.mul(A0, B, C, n, k, n, opts={"product": 1})
+            torch.cuda.synchronize()
+            checks["product_freivalds"] = _freivalds(A0.cpu().numpy().view("uint64"), B.cpu().numpy().view("uint64"),
+                                                     C.cpu().numpy().view("uint64"), n, k, n)
+            del B, C
+        results[variant] = {}
+        for name, o in methods.items():
+            rank = torch.empty(1, dtype=torch.int64, device=dev)
+            ms = _timed(lambda: gf2.pls(A, n, rank=rank, opts=o), steps, 1, pre=lambda: A.copy_(A0))
+            results[variant][name] = {"ms": ms, "rank": int(rank.item())}
+        torch.cuda.empty_cache()
+    gf2.prof_enable(0)
+    clocks = sampler.stop()
+    best = results["dense"]["mmpf"]["ms"]
+    speed = {v: {"rec_tc_over_rec_xor": r["rec_xor"]["ms"] / r["rec_tc"]["ms"],
+                 "mmpf_over_rec_xor": r["rec_xor"]["ms"] / r["mmpf"]["ms"]} for v, r in results.items()}
+    _base_line(args, best / 1e3, "s", best,
+               {"workload": "65536x65536 GF(2): dense Bernoulli(1/2), A=B.C (B 65536x32768, C 32768x65536), "
+                            "Bernoulli(0.01); gf2_pls by MMPF panels and by the recursive PLS (cutoff 4096 columns) "
+                            "with XOR-table and tensor-core products", "m": n, "n": n, "seed": SEED,
+                "value_is": "dense, MMPF"},
+               clocks, gf2.prof_launches(),
+               {"results_ms": results, "speedups": speed, "checks": checks,
+                "bitops_per_s_dense_mmpf": effective_bitops(n, n, results["dense"]["mmpf"]["rank"]) / (best / 1e3)})
+    return 0
+
+
+def run_config4(args):
+    """2048 independent matrices in one gf2_pls_batched call (shapes and densities of the batch recipe),
+    against the same matrices through gf2_pls one by one."""
+    import torch
+    from paper_1006_1744_gb300 import build, gf2, synth, synth_gpu
+    build.build()
+    dev = torch.device("cuda", 0)
+    rec = synth.batch_recipe(2048, SEED)
+    mats0, ns = [], []
+    for (m, n, p, sd) in rec:
+        D = torch.empty((m, synth.default_stride(n)), dtype=torch.int64, device=dev)
+        synth_gpu.fill(D, n, sd, p=p)
+        mats0.append(D)
+        ns.append(n)
+    mats = [x.clone() for x in mats0]
+    shapes = [(m, n, synth.default_stride(n)) for (m, n, p, sd) in rec]
+    nb = gf2.pls_batched_workspace_bytes(shapes)
+    work = torch.empty(nb // 8 + 64, dtype=torch.int64, device=dev)
+    Ps = [torch.empty(m, dtype=torch.int64, device=dev) for (m, *_r) in rec]
+    Qs = [torch.empty(n, dtype=torch.int64, device=dev) for n in ns]
+    ranks = torch.empty(len(rec), dtype=torch.int64, device=dev)
+
+    def restore():
+        for a, b in zip(mats, mats0):
+            a.copy_(b)
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    gf2.prof_reset()
+    gf2.prof_enable(1)
+    per_tile = {}
+    for tw in (8, 4):
+        per_tile[tw] = _timed(lambda: gf2.pls_batched(mats, ns, Ps, Qs, ranks, work=work, opts={"tile_words": tw}),
+                              args.steps, args.warmup, pre=restore)
+    launches = gf2.prof_launches()
+    gf2.prof_enable(0)
+    clocks = sampler.stop()
+    rank_sum = int(ranks.sum().item())
+    # the same matrices one call each (one timed pass)
+    w1 = gf2.new_workspace(gf2.OP_PLS, max(m for m, *_r in rec), max(ns))
+    r1 = torch.empty(len(rec), dtype=torch.int64, device=dev)
+
+    def loop():
+        for i in range(len(rec)):
+            gf2.pls(mats[i], ns[i], Ps[i], Qs[i], r1[i:i + 1], work=w1)
+
+    loop_ms = _timed(loop, 1, 1, pre=restore)
+    best_tw = min(per_tile, key=per_tile.get)
+    best = per_tile[best_tw]
+    total_bytes = sum(m * synth.default_stride(n) * 8 for (m, n, p, sd) in rec)
+    _base_line(args, best / 1e3, "s", best,
+               {"workload": "2048 GF(2) matrices in one gf2_pls_batched call: rows log-uniform in [256, 8192], "
+                            "cols = rows x U[0.5, 2] rounded to 64, density from {0.5, 0.1, 0.01}",
+                "matrices": len(rec), "bytes": total_bytes, "seed": SEED, "value_is": "seconds per batch"},
+               clocks, launches,
+               {"matrices_per_s": len(rec) / (best / 1e3), "ms_by_tile_words": per_tile, "tile_words": best_tw,
+                "loop_of_gf2_pls_ms": loop_ms, "speedup_vs_loop": loop_ms / best,
+                "rank_sum": rank_sum, "ranks_equal_to_loop": bool((r1 == ranks).all().item())})
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gf2", choices=["gf2", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--tile-words", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4],
+                    help="2: the headline line (default); 3: 65536^2 matrices, MMPF vs recursive PLS with "
+                         "XOR-table and tensor-core products; 4: batched PLS of 2048 matrices")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.config == 3:
+        return run_config3(args)
+    if args.config == 4:
+        return run_config4(args)
 
     import numpy as np
     import torch
@@ -227,11 +426,11 @@ def main():
     pls_ms = ev[0].elapsed_time(ev[1])
     rref_ms = ev[2].elapsed_time(ev[3])
 
-    # ---- timed region ----------------------------------------------------------------
+    # ---- timed region (launches counted on the host, no events inside the steps) -------
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     gf2.prof_reset()
-    gf2.prof_enable(3)
+    gf2.prof_enable(1)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if world > 1:
@@ -251,15 +450,23 @@ def main():
     clocks = sampler.stop()
     step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
     launches = gf2.prof_launches()
+
+    # ---- per-kernel-class times: separate untimed steps with an event pair around each
+    # launch of the timed classes, on the stream it runs on ----------------------------
+    prof_steps = 3
+    gf2.prof_reset()
+    gf2.prof_enable(3)
+    for _ in range(prof_steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    gf2.prof_enable(0)
     sweep_ms, sweep_n = gf2.prof_collect(gf2.PROF_SWEEP)
     pivot_ms, pivot_n = gf2.prof_collect(gf2.PROF_PIVOT)
     rref_blk_ms, rref_blk_n = gf2.prof_collect(gf2.PROF_RREF)
     gf2.prof_reset()
 
-    t = torch.tensor([step_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    step_ms_max = float(t.item())
+    step_ms_max = max_over_ranks(step_ms, world, dev)
 
     rank_val = int(r1.item())
     assert rank_val == int(r2.item())
@@ -268,7 +475,7 @@ def main():
     q = Q[:rank_val].cpu().numpy()
     rb = np.searchsorted(q, 64 * np.arange(W))
     sweep_bytes_one = float(np.sum((m - rb).clip(min=0) * (W - np.arange(W)) * 16.0))
-    sweep_bytes = 2 * sweep_bytes_one * args.steps  # both calls run the elimination
+    sweep_bytes = 2 * sweep_bytes_one * prof_steps  # both calls run the elimination
     hbm, peak_kind = peaks()
     shares = {"sweep": sweep_ms, "pivot": pivot_ms, "rref_block": rref_blk_ms}
     tot = sum(shares.values()) or 1.0
@@ -317,13 +524,11 @@ def main():
             e2e_step()
         ee.record()
         torch.cuda.synchronize()
-        te = torch.tensor([es.elapsed_time(ee) / args.steps], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        te_ms = max_over_ranks(es.elapsed_time(ee) / args.steps, world, dev)
         bi = m * stride * 8
         bo = 2 * m * stride * 8 + (m + 2 * n + 2) * 8
-        e2e = {"value": float(te.item()) / 1e3 / world, "unit": "s", "h2d_bytes_per_step": bi,
-               "d2h_bytes_per_step": bo, "ms_per_step": float(te.item())}
+        e2e = {"value": job_seconds_per_matrix(te_ms, world), "unit": "s", "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bo, "ms_per_step": te_ms}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -335,7 +540,7 @@ def main():
         dist.destroy_process_group()
     if rank != 0:
         return 0
-    value = step_ms_max / 1e3 / world
+    value = job_seconds_per_matrix(step_ms_max, world)
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": False, "scaling": "weak",

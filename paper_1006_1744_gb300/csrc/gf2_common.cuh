@@ -23,7 +23,9 @@ struct PanelState {
     int kbar;       // pivots found in the current panel (0..64)
     int status;     // sticky device-side error code (0 = ok)
     int zero_tail;  // 1 once every remaining row is zero in every remaining column
-    int pad0[3];
+    int nz;         // set by this panel's sweep when it found no pivot but a nonzero word right of
+                    // the panel in a trailing row (checked only then)
+    int pad0[2];
     u64 J;          // pivot columns of the panel, as a bit mask of the panel word
     int prow[64];   // physical row of pivot t (rows are never moved during elimination)
     int pcol[64];   // panel-relative column of pivot t

@@ -45,6 +45,7 @@ __global__ void k_init(const uint64_t *__restrict__ A, int64_t stride, int *__re
         st[i].kbar = 0;
         st[i].status = 0;
         st[i].zero_tail = 0;
+        st[i].nz = 0;
         st[i].J = 0;
     }
 }
@@ -574,7 +575,11 @@ __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int6
     __shared__ int sT, sFast;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = st_prev->r_next;
-    const int nwin = (r < m && !st_prev->zero_tail) ? min(WIN, m - r) : 0;
+    // Zero tail: the sweep of panel b - 2 (complete: this search waits for it) found no
+    // pivot and no nonzero word right of it in any trailing row, so no later panel has a
+    // pivot. st still holds panel b - 2's state here (this search overwrites it below).
+    const int zt = st_prev->zero_tail || (b >= 2 && st->kbar == 0 && st->nz == 0 && st->r_next == r);
+    const int nwin = (r < m && !zt) ? min(WIN, m - r) : 0;
     const WordCtx wc{A, stride, b > 0 ? side_prev : nullptr, b};
     // window rows: the previous panel's order where it changed it, perm elsewhere
     // (one row per thread; nwin <= PIVOT_THREADS)
@@ -719,6 +724,8 @@ __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int6
         st->J = J;
         st->nwin = nwin;
         st->nx = S.nx;
+        st->zero_tail = zt;
+        st->nz = 0;
     }
 }
 
@@ -842,13 +849,27 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
         return;
     const int tid = threadIdx.x;
     if (kbar == 0) {
-        // no pivot: every trailing row's panel word is zero; word b + 1 is unchanged
+        // no pivot: every trailing row's panel word is zero; word b + 1 is unchanged. Unless
+        // the tail is already known to be zero, look for a nonzero word right of the panel
+        // in any trailing row (none means no later panel has a pivot).
+        const bool check = !st->zero_tail;
+        bool nzw = false;
         for (int p = r + cta * NT + tid; p < m; p += ncta * NT) {
             const int ph = trailing_row(perm, st, r, nwin, nx, p);
+            const uint64_t *row = A + (int64_t)ph * stride;
             A[(int64_t)ph * stride + b] = side_cur[ph];
-            if (b + 1 < W)
-                side_nxt[ph] = A[(int64_t)ph * stride + b + 1];
+            if (b + 1 < W) {
+                const u64 v = row[b + 1];
+                side_nxt[ph] = v;
+                if (check) {
+                    nzw = nzw || v != 0;
+                    for (int w = b + 2; w < W && !nzw; ++w)
+                        nzw = row[w] != 0;
+                }
+            }
         }
+        if (__syncthreads_or(nzw) && tid == 0)
+            atomicExch(const_cast<int *>(&st->nz), 1);
         return;
     }
     const int wstart = b & ~1;
@@ -1243,6 +1264,7 @@ __global__ void k_init_b(const gf2::ElimDesc *__restrict__ D)
         d.st[g].kbar = 0;
         d.st[g].status = 0;
         d.st[g].zero_tail = 0;
+        d.st[g].nz = 0;
         d.st[g].J = 0;
     }
 }
