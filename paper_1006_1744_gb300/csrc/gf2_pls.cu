@@ -22,7 +22,7 @@
 
 namespace {
 
-constexpr int WIN = 128;   // rows held by the pivot warp (4 per lane)
+constexpr int WIN = 96;    // rows held by the pivot warp (3 per lane)
 constexpr int NSLOT = WIN / 32;
 
 // ---------------------------------------------------------------------------
@@ -65,13 +65,14 @@ __global__ void k_init(const uint64_t *__restrict__ A, int64_t stride, int *__re
 // reduced rows at the pivot columns), which turns the raw panel word of any
 // later row into its multipliers.
 //
-// Fast path (pivot_fast): the first WIN = 128 positions in column form. Lane l
-// holds columns l and l+32 as 128-bit vectors over the positions, so a pivot
-// costs one shuffle of the pivot column, a swap of two bits and a masked XOR
-// per column; the Gauss-Jordan bits of the pivot rows give the columns of
-// U_J^-1 as a by-product. If a column has no candidate in the window while
-// rows exist past it, the panel is redone by the row-form path (pivot_rows),
-// which also scans past the window.
+// Fast path (pivot_fast): the first WIN = 96 positions. Lane l holds the rows at
+// initial positions l, l + 32, l + 64 and their current positions; a pivot costs
+// one warp min-reduction of (position, slot, lane) over the candidates, one
+// shuffle of the pivot row, a relabel of two positions (the swap) and a masked
+// XOR per row. L^-1 and U_J^-1 follow from the pivot rows after the loop. A
+// dense panel needs about 66 rows; if a column has no candidate in the window
+// while rows exist past it, the panel is redone by the row-form path
+// (pivot_rows), which also scans past the window.
 // ---------------------------------------------------------------------------
 constexpr int GROUP = 8;  // columns per group step of the row-form path
 constexpr int SW = 16;    // rows of the prefix eliminated per group step
@@ -195,7 +196,10 @@ __device__ bool pivot_fast(int r, int m, int nwin, int nbits, int &t_out, u64 &J
             continue;
         }
         const int p = best >> 7, slot = (best >> 5) & 3, plane = best & 31;
-        const u64 mine = slot == 0 ? row[0] : slot == 1 ? row[1] : slot == 2 ? row[2] : row[3];
+        u64 mine = row[0];
+#pragma unroll
+        for (int k = 1; k < NSLOT; ++k)
+            mine = slot == k ? row[k] : mine;
         const u64 prow = __shfl_sync(GF2_FULL, mine, plane);
         if (t < 32) {
             nw0 = lane == t ? prow : nw0;
