@@ -214,6 +214,23 @@ int gf2_sync_status(void *stream);
  */
 int gf2_diag_wait_timeout(uint64_t limit_ns, void *stream);
 
+/*
+ * Autotuner (not part of the method; no knob changes a result). Times the
+ * candidate settings of gf2_opts for `op` on a seeded synthetic m x n matrix of
+ * Bernoulli(density) bits on the current device, on `stream`, and returns the
+ * fastest in *best (and its mean time in *ms_out, nullable). Host-blocking; it
+ * allocates and frees its own device buffers. Candidates:
+ *   GF2_OP_PLS / RREF / RANK: tile_words 4, 8 and 16; for PLS with n > 8192 also
+ *     the recursive split at 4096 columns with the XOR-table and the
+ *     tensor-core product;
+ *   GF2_OP_MUL (C = A.B with A m x n, B n x n): the XOR-table and the
+ *     tensor-core product.
+ * The answer is cached per (device, op, ceil(log2 m), ceil(log2 n), density
+ * bucket {>= 0.3, >= 0.03, less}); a repeated call returns it without timing.
+ * GF2_EINVAL for bad arguments, GF2_ENOMEM if no candidate fits in memory.
+ */
+int gf2_autotune(int op, int64_t m, int64_t n, double density, gf2_opts *best, double *ms_out, void *stream);
+
 /* Human-readable text for a GF2_* code (static storage). */
 const char *gf2_strerror(int code);
 

@@ -227,13 +227,29 @@ int gf2_pls_batched(const gf2_batch_item *items, int64_t count, int64_t *ranks, 
         if ((rc = gf2::batch_init(dD + c0, cn, L.max_m, s)))
             return rc;
     }
+    // Pivot searches on s, sweeps on a side stream t: the sweeps of step b overlap the
+    // pivot searches of step b + 1, which wait for the sweeps of step b - 1 (the same
+    // ordering as the single-matrix elimination, for every matrix at once).
+    cudaStream_t t = nullptr;
+    gf2::EventSet E;
+    if ((rc = gf2::side_stream(&t)) || (rc = E.create()))
+        return rc;
+    cudaEvent_t ev_piv = E.ev[0], ev_rest[2] = {E.ev[1], E.ev[2]};
     for (int b = 0; b < L.Wmax; ++b) {
+        if (b >= 2 && (rc = gf2::note_cuda(cudaStreamWaitEvent(s, ev_rest[b & 1], 0))))
+            return rc;
         if ((rc = gf2::batch_pivot(dD, dIdx + step_idx_off[b], step_nact[b], b, s)))
             return rc;
+        if ((rc = gf2::note_cuda(cudaEventRecord(ev_piv, s))) || (rc = gf2::note_cuda(cudaStreamWaitEvent(t, ev_piv, 0))))
+            return rc;
         if ((rc = gf2::batch_sweep(dD, dIdx + step_idx_off[b], dPre + step_pre_off[b], step_nact[b], step_total[b], b,
-                                   tw, s)))
+                                   tw, t)))
+            return rc;
+        if ((rc = gf2::note_cuda(cudaEventRecord(ev_rest[b & 1], t))))
             return rc;
     }
+    if (L.Wmax > 0 && (rc = gf2::note_cuda(cudaStreamWaitEvent(s, ev_rest[(L.Wmax - 1) & 1], 0))))
+        return rc;
     for (int64_t c0 = 0; c0 < count; c0 += 65535) {
         const int cn = (int)(count - c0 < 65535 ? count - c0 : 65535);
         if ((rc = gf2::batch_finish(dD + c0, cn, L.max_m, s)))

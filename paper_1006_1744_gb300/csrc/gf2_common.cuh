@@ -130,12 +130,39 @@ __device__ __forceinline__ void record_status(int *status, int code)
 namespace gf2 {
 
 int *status_word();  // device address of this device's status word (nullptr on failure)
+int note_cuda(cudaError_t e);  // records e for gf2_last_cuda_error, returns GF2_ECUDA or GF2_OK
+
+// a side stream of the current device for overlapped work (gf2_pls.cu)
+int side_stream(cudaStream_t *out);
+
+// events that order two streams within one call, released when the call returns
+struct EventSet {
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    EventSet() = default;
+    EventSet(const EventSet &) = delete;
+    EventSet &operator=(const EventSet &) = delete;
+    ~EventSet()
+    {
+        for (cudaEvent_t x : ev)
+            if (x)
+                cudaEventDestroy(x);  // released once the recorded work completes
+    }
+    int create()
+    {
+        for (cudaEvent_t &x : ev) {
+            cudaError_t err = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+            if (err != cudaSuccess)
+                return note_cuda(err);
+        }
+        return GF2_OK;
+    }
+};
+
 // argument checks and the internal per-device workspace (gf2_api.cu)
 int get_work(void *&work, size_t &work_bytes, size_t need);  // caller's work if given, else the internal one
 int check_mat(const void *A, int64_t m, int64_t n, int64_t stride);
 int check_opts(const gf2_opts *o);
 
-int note_cuda(cudaError_t e);  // records e for gf2_last_cuda_error, returns GF2_ECUDA or GF2_OK
 void prof_launched(int count);              // counts kernel launches when profiling is on
 int prof_begin(cudaStream_t s);             // event before a timed launch (-1: profiling off)
 void prof_end(cudaStream_t s, int cls, int token);

@@ -1429,8 +1429,7 @@ int identity_fill(int64_t *P, int64_t m, int64_t *Q, int64_t n, int64_t *rank, c
     return note_cuda(cudaGetLastError());
 }
 
-// Side streams for the look-ahead (a few per device, created on first use) and
-// the events that order the two streams of one elimination.
+// Side streams for the look-ahead: a few per device, created on first use.
 struct SideStreams {
     std::mutex mu;
     cudaStream_t s[64][4] = {};
@@ -1438,7 +1437,7 @@ struct SideStreams {
 };
 static SideStreams g_side;
 
-static int side_stream(cudaStream_t *out)
+int side_stream(cudaStream_t *out)
 {
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
@@ -1453,25 +1452,6 @@ static int side_stream(cudaStream_t *out)
     *out = g_side.s[dev][k];
     return GF2_OK;
 }
-
-struct EventSet {
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    ~EventSet()
-    {
-        for (cudaEvent_t x : ev)
-            if (x)
-                cudaEventDestroy(x);  // released once the recorded work completes
-    }
-    int create()
-    {
-        for (cudaEvent_t &x : ev) {
-            cudaError_t err = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
-            if (err != cudaSuccess)
-                return note_cuda(err);
-        }
-        return GF2_OK;
-    }
-};
 
 // Panel elimination with a look-ahead of one panel. The pivot searches run on
 // stream s, the table sweeps on the side stream t: the sweep of panel b starts

@@ -59,6 +59,7 @@ SYMBOLS = {
     "gf2_rank_noalloc": (_int, [_vp, _i64, _i64, _i64, _vp, _vp]),
     "gf2_pls_batched_workspace_bytes": (_sz, [_vp, _i64, _vp]),
     "gf2_pls_batched": (_int, [_vp, _i64, _vp, _vp, _sz, _vp, _vp]),
+    "gf2_autotune": (_int, [_int, _i64, _i64, ctypes.c_double, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_double), _vp]),
     "gf2_sync_status": (_int, [_vp]),
     "gf2_diag_wait_timeout": (_int, [ctypes.c_uint64, _vp]),
     "gf2_prof_enable": (None, [_int]),
@@ -266,3 +267,13 @@ def pls_batched(mats, ns, Ps=None, Qs=None, ranks=None, work=None, opts=None, st
     _check(lib().gf2_pls_batched(items, len(mats), _ptr(ranks), wp, wb, _opts(opts), _stream(stream)),
            "gf2_pls_batched")
     return Ps, Qs, ranks
+
+
+def autotune(op: int, m: int, n: int, density: float = 0.5, stream=None):
+    """Fastest gf2_opts for op on an m x n matrix of the given density (cached per size bucket).
+    Returns (opts as a dict, mean milliseconds)."""
+    best = Opts()
+    ms = ctypes.c_double(0.0)
+    _check(lib().gf2_autotune(op, m, n, float(density), ctypes.byref(best), ctypes.byref(ms), _stream(stream)),
+           "gf2_autotune")
+    return {"tile_words": best.tile_words, "cutoff_cols": best.cutoff_cols, "product": best.product}, ms.value

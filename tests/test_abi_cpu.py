@@ -125,3 +125,16 @@ def test_batched_workspace_and_checks_host_only(built):
 def test_status_codes_have_text(built):
     from paper_1006_1744_gb300 import gf2
     assert b"wait" in gf2.lib().gf2_strerror(8)
+
+
+def test_autotune_argument_checks_host_only(built):
+    from paper_1006_1744_gb300 import gf2
+    L = gf2.lib()
+    o = gf2.Opts()
+    ms = __import__("ctypes").c_double()
+    byref = __import__("ctypes").byref
+    assert L.gf2_autotune(99, 64, 64, 0.5, byref(o), byref(ms), None) == 1
+    assert L.gf2_autotune(gf2.OP_PLS, 0, 64, 0.5, byref(o), byref(ms), None) == 1
+    assert L.gf2_autotune(gf2.OP_PLS, 64, 64, 0.0, byref(o), byref(ms), None) == 1
+    assert L.gf2_autotune(gf2.OP_PLS, 64, 64, 1.5, byref(o), byref(ms), None) == 1
+    assert L.gf2_autotune(gf2.OP_PLS, 64, 64, 0.5, None, byref(ms), None) == 1

@@ -318,3 +318,25 @@ def test_pls_batched_many_small_and_user_workspace(g):
             assert (Ps[i].cpu().numpy()[:m] == P[:m]).all()
             assert (Qs[i].cpu().numpy()[:n] == Q[:n]).all()
             assert (host(ds[i])[:, :S.words_per_row(n)] == R[:, :S.words_per_row(n)]).all()
+
+
+def test_autotune_choices_are_exact_and_cached(g):
+    """The autotuner only picks among settings that change no result: PLS with its
+    choice matches the oracle, and a second call returns the cached choice."""
+    m, n = 1500, 2100
+    o1, ms1 = g.autotune(g.OP_PLS, m, n, 0.5)
+    assert o1["tile_words"] in (4, 8, 16) and ms1 > 0
+    o2, ms2 = g.autotune(g.OP_PLS, m, n, 0.5)
+    assert (o1, ms1) == (o2, ms2)
+    check_pls(g, S.dense(m, n, 77), m, n, opts=o1)
+    om, _ = g.autotune(g.OP_MUL, 1024, 1024, 0.5)
+    assert om["product"] in (1, 2)
+    rng = np.random.default_rng(9)
+    A = S.dense(300, 1024, int(rng.integers(1 << 30)))
+    B = S.dense(1024, 700, int(rng.integers(1 << 30)))
+    want = oracle.mul(A, B, 300, 1024, 700)
+    C = torch.zeros((300, S.default_stride(700)), dtype=torch.int64, device="cuda")
+    g.mul(C, dev(A), dev(B), 300, 1024, 700, opts=om)
+    torch.cuda.synchronize()
+    assert (host(C)[:, :11] == want[:, :11]).all()
+    assert g.sync_status() == 0
