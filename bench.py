@@ -314,7 +314,7 @@ def run_config4(args):
     gf2.prof_reset()
     gf2.prof_enable(1)
     per_tile = {}
-    for tw in (8, 4):
+    for tw in (16, 8, 4):
         per_tile[tw] = _timed(lambda: gf2.pls_batched(mats, ns, Ps, Qs, ranks, work=work, opts={"tile_words": tw}),
                               args.steps, args.warmup, pre=restore)
     launches = gf2.prof_launches()

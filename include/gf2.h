@@ -87,9 +87,11 @@ typedef struct gf2_opts {
 } gf2_opts;
 
 /*
- * Bytes of workspace an operation needs for an m x n matrix (for GF2_OP_MUL,
- * m x n is the shape of C and the inner dimension does not matter). Returns 0
- * for invalid sizes.
+ * Bytes of workspace an operation needs for an m x n matrix. For GF2_OP_MUL
+ * pass the inner dimension k as m and the column count n as n: the tensor-core
+ * product keeps B transposed there (n x ceil(k/64) words, rounded to whole
+ * 128-bit chunks); the XOR-table product needs none. Returns 0 for invalid
+ * sizes.
  */
 size_t gf2_workspace_bytes(int op, int64_t m, int64_t n, const gf2_opts *opts);
 

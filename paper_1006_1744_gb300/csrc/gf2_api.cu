@@ -213,8 +213,8 @@ size_t gf2_workspace_bytes(int op, int64_t m, int64_t n, const gf2_opts *opts)
     case GF2_OP_RREF:
     case GF2_OP_RANK:
         return elim_layout(op, m, n).total;
-    case GF2_OP_MUL:
-        return align_up(mul_tensor_workspace(m, 0, n), 256);
+    case GF2_OP_MUL:  // (m, n) = (inner dimension k, columns n)
+        return align_up(mul_tensor_workspace(0, m, n), 256);
     default:
         return 0;
     }

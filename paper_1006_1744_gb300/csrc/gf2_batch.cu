@@ -147,7 +147,7 @@ int gf2_pls_batched(const gf2_batch_item *items, int64_t count, int64_t *ranks, 
     if ((rc = gf2::get_work(work, work_bytes, L.total)))
         return rc;
     char *w = (char *)work;
-    const int tw = (opts && opts->tile_words == 4) ? 4 : 8;
+    const int tw = (opts && opts->tile_words) ? opts->tile_words : 16;
 
     // host image of descriptors + plan, uploaded in one copy
     std::vector<char> img(L.mats);

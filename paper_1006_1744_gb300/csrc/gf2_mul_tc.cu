@@ -7,39 +7,48 @@
 // products is an integer and its parity is the GF(2) dot product. (sm_103a has
 // no 8-bit integer MMA.) To keep every sum far inside the range the
 // accumulator holds exactly, the inner dimension is cut into segments of at
-// most `seg` chunks; after each segment the parities are folded into registers
-// and the accumulator restarts from zero.
+// most `seg` chunks whose parities are folded into registers.
 //
-// Per CTA: a 128 x 256 tile of C, accumulated in 256 TMEM columns. For every
-// 128-bit chunk of the inner dimension, eight warps expand the A tile
-// (128 rows x 128 bits) and the B tile (128 x 256 bits, transposed by warp
-// butterflies into 256 rows x 128 bits) to bytes in shared memory, in the
-// canonical K-major layout without swizzle (core matrices of 8 rows x 16
-// bytes); one thread then issues four MMAs of K = 32 and commits them to the
-// stage's mbarrier. Two stages: expanding chunk c + 1 overlaps the MMAs of
-// chunk c. Every wait is bounded: one that gives up records GF2_ETIMEOUT in the
-// status word and the CTA returns without writing C.
+// Per CTA: a 128 x 256 tile of C, warp-specialised:
+//   warps 0-7   expand 128-bit chunks of A (128 rows) and of B^T (256 rows; B
+//               is transposed once per product into the workspace) to e4m3
+//               bytes in shared memory, in the K-major layout with the 128-byte
+//               swizzle, into a ring of STAGES buffers;
+//   warp 8      (one thread) issues four MMAs of K = 32 per chunk into one of
+//               two TMEM accumulators (256 columns each) -- one per segment,
+//               alternating -- and commits them to the stage's "empty" barrier
+//               and, at a segment's end, to that accumulator's "full" barrier;
+//   warps 9-12  fold a finished segment's parities into registers (their TMEM
+//               lane quarter each) while the next segment accumulates, then
+//               write C.
+// Every wait is bounded: one that gives up records GF2_ETIMEOUT in the status
+// word and the CTA returns without writing C.
 #include "gf2_common.cuh"
 
 namespace {
 
-constexpr int TM = 128;                  // rows of C per CTA (MMA M)
-constexpr int TN = 256;                  // columns of C per CTA (MMA N)
-constexpr int KC = 128;                  // inner-dimension bits per chunk (= bytes per expanded row)
-constexpr int NTHR = 256;                // eight warps
-constexpr int A_BYTES = TM * KC;         // 16 KB
-constexpr int B_BYTES = TN * KC;         // 32 KB
-constexpr int STAGE = A_BYTES + B_BYTES; // 48 KB
-constexpr int SMEM = 2 * STAGE + 1024 + 4096;  // two stages, alignment and tail slack
-constexpr int DEFAULT_SEG = 64;          // chunks per accumulation segment: sums stay <= 8192
+constexpr int TM = 128;                   // rows of C per CTA (MMA M)
+constexpr int TN = 256;                   // columns of C per CTA (MMA N)
+constexpr int KC = 128;                   // inner-dimension bits per chunk (= bytes per expanded row)
+constexpr int STAGES = 4;                 // shared-memory ring
+constexpr int NPROD = 8;                  // producer warps
+constexpr int MMA_WARP = NPROD;           // warp 8
+constexpr int NTHR = (NPROD + 1 + 4) * 32;
+constexpr int A_BYTES = TM * KC;          // 16 KB
+constexpr int B_BYTES = TN * KC;          // 32 KB
+constexpr int STAGE = A_BYTES + B_BYTES;  // 48 KB
+constexpr int SMEM = STAGES * STAGE + 1024 + 4096;  // ring, alignment and tail slack
+constexpr int DEFAULT_SEG = 64;           // chunks per accumulation segment: sums stay <= 8192
 
-// four bits -> four bytes of 0x00 / 0x38 (e4m3 1.0); bit i -> byte i
-__device__ __forceinline__ unsigned expand4(unsigned nib)
-{
-    return ((nib * 0x00204081u) & 0x01010101u) * 0x38u;
-}
+// A 1 bit becomes the e4m3 byte 0x08 (2^-6), a 0 bit 0x00; a product of two
+// ones is 2^-12 and a sum of c of them is c * 2^-12, exact in FP32.
+constexpr float ONE_SQ_INV = 4096.0f;  // 1 / (2^-6)^2
 
-// 16 bits -> one 16-byte core-matrix row
+// four bits -> four bytes (bit i -> byte i): one multiply spreads bit i to bit
+// 8 i + 3 (the shifted copies do not overlap), one mask keeps those bits
+__device__ __forceinline__ unsigned expand4(unsigned nib) { return (nib * 0x01020408u) & 0x08080808u; }
+
+// 16 bits -> one 16-byte row chunk
 __device__ __forceinline__ void store16(unsigned char *p, unsigned b)
 {
     uint4 v;
@@ -50,16 +59,22 @@ __device__ __forceinline__ void store16(unsigned char *p, unsigned b)
     *reinterpret_cast<uint4 *>(p) = v;
 }
 
-// byte offset of (row, 16-byte column group cg) in the K-major no-swizzle layout:
-// core matrix (row / 8, cg) at (row / 8) * SBO + cg * LBO, row inside it at (row % 8) * 16
-constexpr int LBO = 128;             // next core matrix along K
-constexpr int SBO = (KC / 16) * 128; // next group of 8 rows
-__device__ __forceinline__ int core_off(int row, int cg) { return (row >> 3) * SBO + cg * LBO + (row & 7) * 16; }
+// byte offset of (row, 16-byte column group cg) in the K-major layout with the
+// 128-byte swizzle: each expanded row is one 128-byte swizzle row; rows come in
+// atoms of 8 rows (1024 bytes), and chunk cg of row r sits at chunk cg ^ (r % 8)
+// (the hardware applies the same XOR to the address bits, so stages are
+// 1024-byte aligned)
+constexpr int SBO = 1024;  // next group of 8 rows
+__device__ __forceinline__ int core_off(int row, int cg)
+{
+    return (row >> 3) * SBO + (row & 7) * 128 + ((cg ^ (row & 7)) << 4);
+}
 
-// shared-memory matrix descriptor: start, LBO, SBO (16-byte units), version 1, no swizzle
+// shared-memory matrix descriptor: start, LBO (unused with this swizzle), SBO (16-byte
+// units), version 1, layout 128-byte swizzle
 __device__ __forceinline__ u64 smem_desc(uint32_t saddr)
 {
-    return (u64)((saddr & 0x3FFFFu) >> 4) | ((u64)(LBO >> 4) << 16) | ((u64)(SBO >> 4) << 32) | (1ull << 46);
+    return (u64)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((u64)(SBO >> 4) << 32) | (1ull << 46) | (2ull << 61);
 }
 
 // instruction descriptor: D = F32, A = B = E4M3, both K-major, N = TN, M = TM
@@ -108,45 +123,70 @@ __device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&v)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// parities of this thread's 4 x 32 accumulator columns, XORed into par[]
-__device__ __forceinline__ void fold_parity(uint32_t taddr, int warp, unsigned (&par)[4])
+// B (k x n bits, pitch sb) -> BT (n x k bits, pitch sbt words): 32 x 32 blocks,
+// butterfly transpose across a warp; BT's padding words are zero
+__global__ void k_transpose_bits(const uint64_t *__restrict__ B, int64_t sb, uint64_t *__restrict__ BT,
+                                 int64_t sbt, int k, int n)
 {
-    const uint32_t base = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(128 * (warp >> 2));
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        uint32_t v[32];
-        tmem_ld32(base + 32 * c, v);
-        unsigned bits = 0;
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            bits |= ((unsigned)__float2int_rn(__uint_as_float(v[j])) & 1u) << j;
-        par[c] ^= bits;
+    const int lane = threadIdx.x & 31;
+    const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int kslots = (int)(sbt * 2);  // 32-bit slots per BT row
+    const int kb = (k + 31) / 32, nb = (n + 31) / 32;
+    for (int blk = warp; blk < kslots * nb; blk += nwarps) {
+        const int bk = blk % kslots, bn = blk / kslots;
+        const int row = 32 * bk + lane;  // row of B
+        unsigned x = 0;
+        if (bk < kb && row < k) {
+            const int col = 32 * bn;
+            x = (unsigned)(B[(int64_t)row * sb + (col >> 6)] >> (col & 63));
+        }
+        x = transpose32(x, lane);  // lane c: column 32 bn + c over rows 32 bk .. 32 bk + 31
+        const int ocol = 32 * bn + lane;
+        if (ocol < n)
+            reinterpret_cast<unsigned *>(BT + (int64_t)ocol * sbt)[bk] = x;
     }
 }
 
-__global__ void __launch_bounds__(NTHR, 2)
+__device__ __forceinline__ void mbar_arrive(uint32_t mb)
+{
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(mb) : "memory");
+}
+
+__global__ void __launch_bounds__(NTHR, 1)
 k_mul_tc(uint64_t *__restrict__ C, int64_t sc, const uint64_t *__restrict__ A, int64_t sa,
-         const uint64_t *__restrict__ B, int64_t sb, int m, int k, int n, int acc, int seg, int *__restrict__ status)
+         const uint64_t *__restrict__ B /* B transposed: n x k bits */, int64_t sb, int m, int k, int n, int acc,
+         int seg, int *__restrict__ status)
 {
     extern __shared__ unsigned char smraw[];
-    // 1024-byte aligned stage base
+    // 1024-byte aligned ring
     unsigned char *sm = smraw + ((1024u - ((uint32_t)__cvta_generic_to_shared(smraw) & 1023u)) & 1023u);
     __shared__ uint32_t s_taddr;
-    __shared__ __align__(8) u64 s_mbar[2];
-    __shared__ int s_fail;
+    __shared__ __align__(8) u64 s_full[STAGES], s_empty[STAGES], s_sfull[2], s_sempty[2];
+    __shared__ volatile int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row0 = blockIdx.y * TM, col0 = blockIdx.x * TN;
     const int KW = (k + 63) >> 6, NW = (n + 63) >> 6;
     const int nchunks = (k + KC - 1) / KC;
-    const uint32_t mb0 = (uint32_t)__cvta_generic_to_shared(&s_mbar[0]);
+    const int nseg = (nchunks + seg - 1) / seg;
+    const uint32_t full0 = (uint32_t)__cvta_generic_to_shared(&s_full[0]);
+    const uint32_t empty0 = (uint32_t)__cvta_generic_to_shared(&s_empty[0]);
+    const uint32_t sfull0 = (uint32_t)__cvta_generic_to_shared(&s_sfull[0]);
+    const uint32_t sempty0 = (uint32_t)__cvta_generic_to_shared(&s_sempty[0]);
     if (warp == 0) {
         const uint32_t slot = (uint32_t)__cvta_generic_to_shared(&s_taddr);
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(TN));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(2 * TN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb0), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb0 + 8), "r"(1));
+        for (int i = 0; i < STAGES; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full0 + 8 * i), "r"(NPROD));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(empty0 + 8 * i), "r"(1));
+        }
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sfull0 + 8 * i), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sempty0 + 8 * i), "r"(4));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
     }
@@ -155,142 +195,182 @@ k_mul_tc(uint64_t *__restrict__ C, int64_t sc, const uint64_t *__restrict__ A, i
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t taddr = s_taddr;
     const uint32_t sm_addr = (uint32_t)__cvta_generic_to_shared(sm);
-    unsigned par[4] = {0u, 0u, 0u, 0u};
-    int issued = 0;  // chunks whose MMAs have been issued (and committed)
-    for (int ch = 0; ch < nchunks; ++ch) {
-        const int st = ch & 1;
-        unsigned char *sA = sm + st * STAGE;
-        unsigned char *sB = sA + A_BYTES;
-        // stage st was last read by chunk ch - 2: wait for its commit
-        if (ch >= 2 && !mbar_wait(mb0 + 8 * st, (uint32_t)(((ch >> 1) - 1) & 1)))
-            s_fail = 1;
-        const int w0 = ch * (KC / 64);
-        // A tile: thread -> (row, half): one word of one row, four core rows
-        {
-            const int r = tid & (TM - 1), half = tid >> 7, gr = row0 + r, w = w0 + half;
-            const u64 a = (gr < m && w < KW) ? A[(int64_t)gr * sa + w] : 0ull;
+    unsigned par[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+
+    if (warp < NPROD) {
+        // ---------------- producers: expand chunk c into stage c % STAGES ----------------
+        // The packed words of the next PD chunks are in flight in registers, so a chunk
+        // never waits for its own global loads.
+        constexpr int PD = 4;
+        const int ar = tid & (TM - 1), ahalf = tid >> 7, agr = row0 + ar;
+        const int bgr = col0 + tid;  // row of BT (= column of B) this thread expands
+        u64 qa[PD], qb0[PD], qb1[PD];
+        auto load = [&](int c, u64 &a, u64 &b0, u64 &b1) {
+            const int w = c * (KC / 64);
+            a = (c < nchunks && agr < m && w + ahalf < KW) ? A[(int64_t)agr * sa + w + ahalf] : 0ull;
+            b0 = 0;
+            b1 = 0;
+            if (c < nchunks && bgr < n) {  // BT's pitch is even: both words of a chunk exist
+                const ulonglong2 v2 = *reinterpret_cast<const ulonglong2 *>(B + (int64_t)bgr * sb + w);
+                b0 = v2.x;
+                b1 = v2.y;
+            }
+        };
+#pragma unroll
+        for (int i = 0; i < PD; ++i)
+            load(i, qa[i], qb0[i], qb1[i]);
+        for (int c = 0; c < nchunks && !s_fail; ++c) {
+            const int st = c % STAGES;
+            if (!mbar_wait(empty0 + 8 * st, (uint32_t)(((c / STAGES) & 1) ^ 1))) {
+                s_fail = 1;
+                break;
+            }
+            unsigned char *sA = sm + st * STAGE;
+            unsigned char *sB = sA + A_BYTES;
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                store16(sA + core_off(r, 4 * half + j), (unsigned)(a >> (16 * j)) & 0xFFFFu);
-        }
-        // B tile: 128 rows (inner dimension) x 4 words; warp -> two (row block, word) units
+                store16(sA + core_off(ar, 4 * ahalf + j), (unsigned)(qa[0] >> (16 * j)) & 0xFFFFu);
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int unit = warp * 2 + u;  // 0..15
-            const int kb = unit >> 2, wi = unit & 3;
-            const int krow = ch * KC + 32 * kb + lane;
-            const int wcol = (col0 >> 6) + wi;
-            const u64 b = (krow < k && wcol < NW) ? B[(int64_t)krow * sb + wcol] : 0ull;
-            const unsigned lo = transpose32((unsigned)b, lane);          // column 64 wi + lane
-            const unsigned hi = transpose32((unsigned)(b >> 32), lane);  // column 64 wi + 32 + lane
-            const int r_lo = 64 * wi + lane, r_hi = r_lo + 32;
-            store16(sB + core_off(r_lo, 2 * kb), lo & 0xFFFFu);
-            store16(sB + core_off(r_lo, 2 * kb + 1), lo >> 16);
-            store16(sB + core_off(r_hi, 2 * kb), hi & 0xFFFFu);
-            store16(sB + core_off(r_hi, 2 * kb + 1), hi >> 16);
-        }
-        // generic-proxy writes must be visible to the tensor cores (async proxy)
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (s_fail)
-            break;
-        const bool restart = (ch % seg) == 0;
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a_addr = sm_addr + st * STAGE, b_addr = a_addr + A_BYTES;
-#pragma unroll
-            for (int kk = 0; kk < KC / 32; ++kk) {
-                // K = 32 bytes = two core matrices along K
-                const u64 ad = smem_desc(a_addr + kk * 2 * LBO);
-                const u64 bd = smem_desc(b_addr + kk * 2 * LBO);
-                const uint32_t en = (restart && kk == 0) ? 0u : 1u;
-                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                             "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(taddr),
-                             "l"(ad), "l"(bd), "r"(IDESC), "r"(en)
-                             : "memory");
+            for (int j = 0; j < 4; ++j) {
+                store16(sB + core_off(tid, j), (unsigned)(qb0[0] >> (16 * j)) & 0xFFFFu);
+                store16(sB + core_off(tid, 4 + j), (unsigned)(qb1[0] >> (16 * j)) & 0xFFFFu);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb0 + 8 * st)
-                         : "memory");
-        }
-        issued = ch + 1;
-        // end of a segment: wait for its MMAs, fold the parities, restart the accumulator
-        if ((ch + 1) % seg == 0 && ch + 1 < nchunks) {
-            if (!mbar_wait(mb0 + 8 * st, (uint32_t)((ch >> 1) & 1)))
-                s_fail = 1;
-            __syncthreads();
-            if (s_fail)
-                break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            fold_parity(taddr, warp, par);
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
-        }
-    }
-    // the last commit covers every MMA issued before it; the other stage's last
-    // arrival is awaited too, so that no arrival is still on its way at exit
-    if (issued > 0 && !mbar_wait(mb0 + 8 * ((issued - 1) & 1), (uint32_t)(((issued - 1) >> 1) & 1)))
-        s_fail = 1;
-    if (issued > 1 && !mbar_wait(mb0 + 8 * ((issued - 2) & 1), (uint32_t)(((issued - 2) >> 1) & 1)))
-        s_fail = 1;
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!s_fail) {
-        if (issued > 0)
-            fold_parity(taddr, warp, par);
-        // warp -> TMEM lane quarter (rows) and column half
-        const int r = row0 + 32 * (warp & 3) + lane;
-        if (r < m) {
-            unsigned *crow = reinterpret_cast<unsigned *>(C + (int64_t)r * sc);
+            // generic-proxy writes must be visible to the tensor cores (async proxy)
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(full0 + 8 * st);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int col = col0 + 128 * (warp >> 2) + 32 * c;
-                if (col >= 64 * NW)
-                    continue;
-                unsigned bits = par[c];
-                if (col >= n)
-                    bits = 0;
-                else if (col + 32 > n)
-                    bits &= (1u << (n - col)) - 1u;
-                if (acc)
-                    crow[col >> 5] ^= bits;
-                else
-                    crow[col >> 5] = bits;
+            for (int i = 0; i < PD - 1; ++i) {
+                qa[i] = qa[i + 1];
+                qb0[i] = qb0[i + 1];
+                qb1[i] = qb1[i + 1];
+            }
+            load(c + PD, qa[PD - 1], qb0[PD - 1], qb1[PD - 1]);
+        }
+        // the last stages' release arrivals, so that none lands after the CTA exits
+        for (int c = max(0, nchunks - STAGES); c < nchunks && !s_fail; ++c)
+            if (!mbar_wait(empty0 + 8 * (c % STAGES), (uint32_t)((c / STAGES) & 1)))
+                s_fail = 1;
+    } else if (warp == MMA_WARP) {
+        // ---------------- one thread issues the MMAs ----------------
+        if (lane == 0) {
+            for (int c = 0; c < nchunks && !s_fail; ++c) {
+                const int st = c % STAGES, sg = c / seg, a = sg & 1;
+                const bool first = c % seg == 0;
+                const bool last = c % seg == seg - 1 || c == nchunks - 1;
+                if (first && !mbar_wait(sempty0 + 8 * a, (uint32_t)(((sg >> 1) & 1) ^ 1))) {
+                    s_fail = 1;
+                    break;
+                }
+                if (!mbar_wait(full0 + 8 * st, (uint32_t)((c / STAGES) & 1))) {
+                    s_fail = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a_addr = sm_addr + st * STAGE, b_addr = a_addr + A_BYTES;
+                const uint32_t dst = taddr + (uint32_t)(a * TN);
+#pragma unroll
+                for (int kk = 0; kk < KC / 32; ++kk) {
+                    // K = 32 bytes: the next 32 bytes of every 128-byte row
+                    const u64 ad = smem_desc(a_addr + kk * 32);
+                    const u64 bd = smem_desc(b_addr + kk * 32);
+                    const uint32_t en = (first && kk == 0) ? 0u : 1u;
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(dst),
+                                 "l"(ad), "l"(bd), "r"(IDESC), "r"(en)
+                                 : "memory");
+                }
+                asm volatile(
+                    "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(empty0 + 8 * st)
+                    : "memory");
+                if (last)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     sfull0 + 8 * a)
+                                 : "memory");
+            }
+        }
+    } else {
+        // ---------------- epilogue: fold every segment, then write C ----------------
+        const int q = warp & 3;  // TMEM lane quarter = rows 32 q .. 32 q + 31
+        for (int sg = 0; sg < nseg && !s_fail; ++sg) {
+            const int a = sg & 1;
+            if (!mbar_wait(sfull0 + 8 * a, (uint32_t)((sg >> 1) & 1))) {
+                s_fail = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t base = taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * TN);
+#pragma unroll
+            for (int c32 = 0; c32 < TN / 32; ++c32) {
+                uint32_t v[32];
+                tmem_ld32(base + 32 * c32, v);
+                unsigned bits = 0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    bits |= ((unsigned)__float2int_rn(__uint_as_float(v[j]) * ONE_SQ_INV) & 1u) << j;
+                par[c32] ^= bits;
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(sempty0 + 8 * a);
+        }
+        if (!s_fail && nchunks > 0) {
+            const int r = row0 + 32 * q + lane;
+            if (r < m) {
+                unsigned *crow = reinterpret_cast<unsigned *>(C + (int64_t)r * sc);
+#pragma unroll
+                for (int c32 = 0; c32 < TN / 32; ++c32) {
+                    const int col = col0 + 32 * c32;
+                    if (col >= 64 * NW)
+                        continue;
+                    unsigned bits = par[c32];
+                    if (col >= n)
+                        bits = 0;
+                    else if (col + 32 > n)
+                        bits &= (1u << (n - col)) - 1u;
+                    if (acc)
+                        crow[col >> 5] ^= bits;
+                    else
+                        crow[col >> 5] = bits;
+                }
             }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (s_fail && tid == 0) {
-        record_status(status, GF2_ETIMEOUT);
-        // give the MMAs in flight one more bounded chance to finish before TMEM is freed
-        if (issued > 0)
-            (void)mbar_wait(mb0 + 8 * ((issued - 1) & 1), (uint32_t)(((issued - 1) >> 1) & 1));
-    }
-    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (s_fail && tid == 0)
+        record_status(status, GF2_ETIMEOUT);
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(2 * TN));
 }
 
 }  // namespace
 
 namespace gf2 {
 
+// row pitch (words) of B^T: whole 128-bit chunks
+static int64_t bt_pitch(int64_t k)
+{
+    const int64_t w = (k + 63) / 64;
+    return w < 2 ? 2 : (w + 1) / 2 * 2;
+}
+
 size_t mul_tensor_workspace(int64_t m, int64_t k, int64_t n)
 {
     (void)m;
-    (void)k;
-    (void)n;
-    return 0;  // B is transposed tile by tile inside the kernel
+    return align_up((size_t)n * (size_t)bt_pitch(k) * 8, 256);  // B^T
 }
 
 int mul_tensor(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64_t *B, int64_t sb, int64_t m,
                int64_t k, int64_t n, int acc, void *work, size_t work_bytes, cudaStream_t s)
 {
-    (void)work;
-    (void)work_bytes;
     if (m == 0 || n == 0)
         return GF2_OK;
+    if (k > 0 && (!work || work_bytes < mul_tensor_workspace(m, k, n)))
+        return GF2_ENOSPACE;
     if (k == 0) {
         if (!acc)
             return note_cuda(cudaMemset2DAsync(C, (size_t)sc * 8, 0, (size_t)((n + 63) / 64) * 8, (size_t)m, s));
@@ -306,13 +386,20 @@ int mul_tensor(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uin
     int *status = status_word();
     if (!status)
         return GF2_ECUDA;
+    uint64_t *BT = reinterpret_cast<uint64_t *>(work);
+    const int64_t sbt = bt_pitch(k);
+    k_transpose_bits<<<2 * sm_count(), 256, 0, s>>>(B, sb, BT, sbt, (int)k, (int)n);
+    prof_launched(1);
+    int rc0 = note_cuda(cudaGetLastError());
+    if (rc0)
+        return rc0;
     // grid.y is limited to 65535 row tiles: larger products go in slabs of rows
     constexpr int64_t SLAB = (int64_t)65535 * TM;
     for (int64_t r0 = 0; r0 < m; r0 += SLAB) {
         const int64_t mr = m - r0 < SLAB ? m - r0 : SLAB;
         const dim3 grid((unsigned)((n + TN - 1) / TN), (unsigned)((mr + TM - 1) / TM));
         const int tok = prof_begin(s);
-        k_mul_tc<<<grid, NTHR, SMEM, s>>>(C + r0 * sc, sc, A + r0 * sa, sa, B, sb, (int)mr, (int)k, (int)n, acc,
+        k_mul_tc<<<grid, NTHR, SMEM, s>>>(C + r0 * sc, sc, A + r0 * sa, sa, BT, sbt, (int)mr, (int)k, (int)n, acc,
                                           DEFAULT_SEG, status);
         prof_end(s, GF2_PROF_MUL, tok);
         prof_launched(1);

@@ -1346,7 +1346,7 @@ __global__ void k_copyback_b(const gf2::ElimDesc *__restrict__ D)
 namespace gf2 {
 
 // rows per pass of the batched sweep variants below (threads / threads per row)
-int sweep_rows_per_pass(int tile_words) { return tile_words == 4 ? 512 / 2 : 1024 / 4; }
+int sweep_rows_per_pass(int tile_words) { return tile_words == 4 ? 512 / 2 : tile_words == 16 ? 1024 / 8 : 1024 / 4; }
 int sweep_ctas_per_sm(int tile_words) { return tile_words == 4 ? 2 : 1; }
 
 int batch_init(const ElimDesc *D, int count, int max_m, cudaStream_t s)
@@ -1395,8 +1395,9 @@ int batch_sweep(const ElimDesc *D, const int *idx, const int *pre, int nact, int
 {
     if (nact <= 0 || total <= 0)
         return GF2_OK;
-    return tile_words == 4 ? launch_sweep_b<4, 1, 512, 2>(D, idx, pre, nact, total, b, s)
-                           : launch_sweep_b<8, 1, 1024, 1>(D, idx, pre, nact, total, b, s);
+    return tile_words == 4    ? launch_sweep_b<4, 1, 512, 2>(D, idx, pre, nact, total, b, s)
+           : tile_words == 16 ? launch_sweep_b<16, 1, 1024, 1>(D, idx, pre, nact, total, b, s)
+                              : launch_sweep_b<8, 1, 1024, 1>(D, idx, pre, nact, total, b, s);
 }
 
 int batch_finish(const ElimDesc *D, int count, int max_m, cudaStream_t s)

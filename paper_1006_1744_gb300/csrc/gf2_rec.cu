@@ -292,6 +292,8 @@ struct RecWork {
     int *perms;           // (depth + 2) x m ints
     int64_t *qtmp;        // n + 1 int64
     int64_t *rank1;       // one int64 on the device
+    uint64_t *bt;         // the tensor-core product's B^T (n x (W + 2) words)
+    size_t bt_bytes;
     int64_t m_full;
     int depth_max;
 };
@@ -383,7 +385,7 @@ static int pls_rec(uint64_t *A, int64_t stride, int64_t m, int64_t n, int64_t *P
             const int product = opts->product == GF2_PRODUCT_TENSOR ? GF2_PRODUCT_TENSOR : GF2_PRODUCT_XOR;
             if (product == GF2_PRODUCT_TENSOR)
                 rc = mul_tensor(A1 + r0 * stride, stride, A + r0 * stride, stride, A1, stride, m - r0, r0, n - n0, 1,
-                                nullptr, 0, s);
+                                w.bt, w.bt_bytes, s);
             else
                 rc = mul_xor(A1 + r0 * stride, stride, A + r0 * stride, stride, A1, stride, m - r0, r0, n - n0, 1,
                              opts->tile_words, opts->grid_ctas, s);
@@ -426,6 +428,7 @@ size_t rec_workspace_bytes(int64_t m, int64_t n, int64_t cutoff)
     off += align_up((size_t)(2 * depth + 4) * (size_t)std::max<int64_t>(m, 1) * 4, 256);
     off += align_up((size_t)(n + 1) * 8, 256);
     off += 256;
+    off += align_up((size_t)std::max<int64_t>(n, 1) * (size_t)(W + 2) * 8, 256);
     return off;
 }
 
@@ -452,6 +455,9 @@ int pls_recursive(uint64_t *A, int64_t stride, int64_t m, int64_t n, int64_t *P,
     w.qtmp = reinterpret_cast<int64_t *>(work + off);
     off += align_up((size_t)(n + 1) * 8, 256);
     w.rank1 = reinterpret_cast<int64_t *>(work + off);
+    off += 256;
+    w.bt = reinterpret_cast<uint64_t *>(work + off);
+    w.bt_bytes = align_up((size_t)std::max<int64_t>(n, 1) * (size_t)(W + 2) * 8, 256);
     w.m_full = m;
     w.depth_max = depth;
     int64_t r = 0;

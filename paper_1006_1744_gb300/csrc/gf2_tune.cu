@@ -128,8 +128,9 @@ extern "C" int gf2_autotune(int op, int64_t m, int64_t n, double density, gf2_op
     gf2_opts best_opts{};
     int rc = GF2_OK;
     for (const gf2_opts &o : cands) {
-        const size_t need = gf2_workspace_bytes(op, m, n, &o);  // 0 for the product: it needs none
-        if (!need && op != GF2_OP_MUL) {
+        // the product's workspace is sized by its inner dimension (n here) and columns
+        const size_t need = op == GF2_OP_MUL ? gf2_workspace_bytes(op, n, n, &o) : gf2_workspace_bytes(op, m, n, &o);
+        if (!need) {
             rc = GF2_EINVAL;
             break;
         }
