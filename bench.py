@@ -344,6 +344,109 @@ def run_config4(args):
     return 0
 
 
+def run_config5(args):
+    """Request stream: echelon-structured matrices arriving as a Poisson process at
+    0.5, 0.8 and 1.0 times the measured capacity. Matrices are generated and kept on
+    the device; whenever the GPU is free, every request that has arrived is admitted
+    as long as the batch's workspace fits the budget set from free device memory,
+    and the batch runs as one gf2_pls_batched call. Latency = completion - arrival."""
+    import numpy as np
+    import torch
+    from paper_1006_1744_gb300 import build, gf2, synth, synth_gpu
+    build.build()
+    dev = torch.device("cuda", 0)
+    R = max(16, args.requests)
+    rec = synth.request_recipe(R, SEED)
+    mats0, mats, ns = [], [], []
+    for (m, n, sd) in rec:
+        D = torch.empty((m, synth.default_stride(n)), dtype=torch.int64, device=dev)
+        synth_gpu.fill(D, n, sd, p=0.3, echelon_frac=0.5)
+        mats0.append(D)
+        mats.append(torch.empty_like(D))
+        ns.append(n)
+    Ps = [torch.empty(m, dtype=torch.int64, device=dev) for (m, n, sd) in rec]
+    Qs = [torch.empty(n, dtype=torch.int64, device=dev) for n in ns]
+    ranks = torch.empty(R, dtype=torch.int64, device=dev)
+    shapes = [(m, n, synth.default_stride(n)) for (m, n, sd) in rec]
+    ws_each = [gf2.pls_batched_workspace_bytes([sh]) for sh in shapes]
+    free, _total = torch.cuda.mem_get_info(dev)
+    budget = int(min(free * 0.6, gf2.pls_batched_workspace_bytes(shapes)))
+    work = torch.empty(budget // 8 + 64, dtype=torch.int64, device=dev)
+
+    def run_batch(ids):
+        for i in ids:
+            mats[i].copy_(mats0[i])
+        Pi = [Ps[i] for i in ids]
+        Qi = [Qs[i] for i in ids]
+        rk = torch.empty(len(ids), dtype=torch.int64, device=dev)
+        gf2.pls_batched([mats[i] for i in ids], [ns[i] for i in ids], Pi, Qi, rk, work=work)
+        return rk
+
+    def take(order, start):
+        """Indices from order[start:] while the batch workspace fits the budget."""
+        ids, need = [], 0
+        for i in order[start:]:
+            if ids and need + ws_each[i] > budget:
+                break
+            ids.append(i)
+            need += ws_each[i]
+        return ids
+
+    # capacity: requests per second when everything is queued at once
+    run_batch(take(list(range(R)), 0))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done = 0
+    while done < R:
+        ids = take(list(range(R)), done)
+        rk = run_batch(ids)
+        torch.cuda.synchronize()
+        ranks[done:done + len(ids)] = rk
+        done += len(ids)
+    capacity = R / (time.perf_counter() - t0)
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    gf2.prof_reset()
+    gf2.prof_enable(1)
+    results = {}
+    for frac in (0.5, 0.8, 1.0):
+        lam = frac * capacity
+        arr = synth.arrival_times(R, lam, SEED + int(frac * 100))
+        comp = np.zeros(R)
+        nbatch, nxt = 0, 0
+        start = time.perf_counter()
+        while nxt < R:
+            now = time.perf_counter() - start
+            if arr[nxt] > now:
+                time.sleep(min(arr[nxt] - now, 0.0005))
+                continue
+            arrived = int(np.searchsorted(arr, now, side="right"))
+            ids = take(list(range(arrived)), nxt)
+            run_batch(ids)
+            torch.cuda.synchronize()
+            comp[ids] = time.perf_counter() - start
+            nxt += len(ids)
+            nbatch += 1
+        lat = comp - arr
+        results[f"{frac:.1f}"] = {
+            "rate_per_s": lam, "throughput_per_s": R / comp[-1], "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "batches": nbatch, "mean_batch": R / nbatch}
+    launches = gf2.prof_launches()
+    gf2.prof_enable(0)
+    clocks = sampler.stop()
+    v = results["0.8"]["p99_ms"]
+    _base_line(args, v / 1e3, "s", v,
+               {"workload": "request stream: echelon-structured GF(2) matrices (m log-uniform in [512, 32768], "
+                            "n = m to 2m, row i zero before column 0.5 i n / m, Bernoulli(0.3) after), Poisson "
+                            "arrivals at 0.5, 0.8, 1.0 x capacity, batched as they arrive, PLS + rank",
+                "requests": R, "seed": SEED, "value_is": "p99 latency at 0.8 x capacity",
+                "workspace_budget_bytes": budget},
+               clocks, launches,
+               {"capacity_per_s": capacity, "by_load": results, "rank_sum": int(ranks.sum().item())})
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -354,9 +457,11 @@ def main():
     ap.add_argument("--tile-words", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4],
+    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5],
                     help="2: the headline line (default); 3: 65536^2 matrices, MMPF vs recursive PLS with "
-                         "XOR-table and tensor-core products; 4: batched PLS of 2048 matrices")
+                         "XOR-table and tensor-core products; 4: batched PLS of 2048 matrices; 5: a stream of "
+                         "requests with Poisson arrivals, batched as they arrive")
+    ap.add_argument("--requests", type=int, default=1024, help="config 5: requests per arrival rate")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -365,6 +470,8 @@ def main():
         return run_config3(args)
     if args.config == 4:
         return run_config4(args)
+    if args.config == 5:
+        return run_config5(args)
 
     import numpy as np
     import torch

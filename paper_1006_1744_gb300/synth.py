@@ -171,3 +171,24 @@ def batch_recipe(count: int, base_seed: int):
         p = (0.5, 0.1, 0.01)[min(2, int(3 * _unit(s, 3)))]
         out.append((m, n, p, s))
     return out
+
+
+def request_recipe(count: int, base_seed: int):
+    """Shapes of a stream of requests (the request-stream workload): m =
+    floor(exp(U[ln 512, ln 32768])), n = 64 * ceil(m * U[1, 2] / 64), row i zero
+    before column floor(0.5 i n / m) and Bernoulli(0.3) after it; seed of request
+    i = mix(base_seed + i). Returns a list of (m, n, seed)."""
+    out = []
+    lo, hi = np.log(512.0), np.log(32768.0)
+    for i in range(count):
+        s = int(mix(_U64((base_seed + 0x5E5E0000 + i) & 0xFFFFFFFFFFFFFFFF)))
+        m = int(np.floor(np.exp(lo + (hi - lo) * _unit(s, 1))))
+        n = 64 * int(np.ceil(m * (1.0 + _unit(s, 2)) / 64))
+        out.append((m, n, s))
+    return out
+
+
+def arrival_times(count: int, rate: float, seed: int) -> np.ndarray:
+    """Poisson arrivals at `rate` per second: cumulative exponential gaps (s)."""
+    u = np.array([_unit(seed, 1000 + i) for i in range(count)])
+    return np.cumsum(-np.log1p(-u) / rate)
