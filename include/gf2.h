@@ -233,6 +233,26 @@ int gf2_diag_wait_timeout(uint64_t limit_ns, void *stream);
  */
 int gf2_autotune(int op, int64_t m, int64_t n, double density, gf2_opts *best, double *ms_out, void *stream);
 
+/*
+ * Replay of repeated calls (not part of the method; no result changes). One
+ * elimination is a few hundred dependent kernel launches on two streams. When
+ * gf2_pls (without the recursive split), gf2_rref or gf2_rank is called again
+ * with exactly the same arguments (pointers, sizes, options, stream, device),
+ * the library captures that call's launches into a CUDA graph and launches the
+ * graph on `stream` from then on; the graph reads the buffers' current
+ * contents, so the results are those of a direct call. The first occurrence of
+ * an argument list runs directly; at most 32 graphs are kept (least recently
+ * used dropped). Calls are never captured while launch timing (gf2_prof_enable
+ * flag 2) is on, while `stream` is itself being captured by the caller (the
+ * launches then go into the caller's graph), or when capture fails.
+ * Freeing a buffer and allocating another at the same address keeps replays
+ * valid. gf2_replay_enable(0) switches replay off (process-wide; default on);
+ * gf2_replay_stats reports how many graphs were captured and how many calls
+ * were replayed since the process started (either pointer may be NULL).
+ */
+void gf2_replay_enable(int on);
+void gf2_replay_stats(long long *captured, long long *replayed);
+
 /* Human-readable text for a GF2_* code (static storage). */
 const char *gf2_strerror(int code);
 

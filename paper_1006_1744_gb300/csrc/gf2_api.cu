@@ -1,4 +1,5 @@
 // gf2_api.cu -- C ABI entry points: argument checks, workspace, dispatch.
+#include <cstring>
 #include <mutex>
 #include <stdint.h>
 #include <stdio.h>
@@ -195,6 +196,28 @@ int pls_base(uint64_t *A, int64_t stride, int64_t m, int64_t n, int64_t *P, int6
     return note_cuda(cudaMemcpyAsync(perm_out, e.perm, (size_t)m * sizeof(int), cudaMemcpyDeviceToDevice, s));
 }
 
+static CallKey call_key(int op, const void *A, int64_t m, int64_t n, int64_t stride, const void *P, const void *Q,
+                        const void *rank, const void *pivots, const void *work, size_t work_bytes, const Elim &e)
+{
+    CallKey k;
+    std::memset(&k, 0, sizeof(k));  // padding too: keys are compared bytewise
+    cudaGetDevice(&k.device);
+    k.op = op;
+    k.tile_words = e.tile_words;
+    k.grid = e.grid;
+    k.A = A;
+    k.m = m;
+    k.n = n;
+    k.stride = stride;
+    k.P = P;
+    k.Q = Q;
+    k.rank = rank;
+    k.pivots = pivots;
+    k.work = work;
+    k.work_bytes = work_bytes;
+    return k;
+}
+
 }  // namespace gf2
 
 using namespace gf2;
@@ -242,12 +265,16 @@ int gf2_pls(uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *P, int64
     const ElimLayout L = elim_layout(GF2_OP_PLS, m, n);
     if ((rc = get_work(work, work_bytes, L.total)))
         return rc;
-    Elim e = make_elim(A, m, n, stride, (char *)work, L, P, Q, true, opts, s);
-    if ((rc = elim_run(e)))
-        return rc;
-    if ((rc = elim_gather(e, rank)))
-        return rc;
-    return pls_finish(e);
+    const Elim e = make_elim(A, m, n, stride, (char *)work, L, P, Q, true, opts, s);
+    return run_replayed(call_key(GF2_OP_PLS, A, m, n, stride, P, Q, rank, nullptr, work, work_bytes, e), s,
+                        [&](cudaStream_t st) {
+                            Elim es = e;
+                            es.s = st;
+                            int r2 = elim_run(es);
+                            if (!r2)
+                                r2 = elim_gather(es, rank);
+                            return r2 ? r2 : pls_finish(es);
+                        });
 }
 
 int gf2_rref(uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *rank, int64_t *pivots, void *work,
@@ -268,10 +295,14 @@ int gf2_rref(uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *rank, i
         return rc;
     char *w = (char *)work;
     int64_t *Qs = reinterpret_cast<int64_t *>(w + q_scratch_offset(L, n));
-    Elim e = make_elim(A, m, n, stride, w, L, nullptr, Qs, true, opts, s);
-    if ((rc = elim_run(e)))
-        return rc;
-    return rref_finish(e, L, w, rank, pivots);
+    const Elim e = make_elim(A, m, n, stride, w, L, nullptr, Qs, true, opts, s);
+    return run_replayed(call_key(GF2_OP_RREF, A, m, n, stride, nullptr, nullptr, rank, pivots, work, work_bytes, e),
+                        s, [&](cudaStream_t st) {
+                            Elim es = e;
+                            es.s = st;
+                            const int r2 = elim_run(es);
+                            return r2 ? r2 : rref_finish(es, L, w, rank, pivots);
+                        });
 }
 
 int gf2_rank(const uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *rank, void *work,
@@ -293,14 +324,19 @@ int gf2_rank(const uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *r
     char *w = (char *)work;
     uint64_t *copy = reinterpret_cast<uint64_t *>(w + L.out);
     const int64_t cs = min_stride(n);
-    cudaError_t err = cudaMemcpy2DAsync(copy, (size_t)cs * 8, A, (size_t)stride * 8, (size_t)((n + 63) / 64) * 8,
-                                        (size_t)m, cudaMemcpyDeviceToDevice, s);
-    if (err != cudaSuccess)
-        return note_cuda(err);
-    Elim e = make_elim(copy, m, n, cs, w, L, nullptr, nullptr, false, opts, s);
-    if ((rc = elim_run(e)))
-        return rc;
-    return elim_gather(e, rank);
+    const Elim e = make_elim(copy, m, n, cs, w, L, nullptr, nullptr, false, opts, s);
+    return run_replayed(call_key(GF2_OP_RANK, A, m, n, stride, nullptr, nullptr, rank, nullptr, work, work_bytes, e),
+                        s, [&](cudaStream_t st) {
+                            cudaError_t err = cudaMemcpy2DAsync(copy, (size_t)cs * 8, A, (size_t)stride * 8,
+                                                                (size_t)((n + 63) / 64) * 8, (size_t)m,
+                                                                cudaMemcpyDeviceToDevice, st);
+                            if (err != cudaSuccess)
+                                return note_cuda(err);
+                            Elim es = e;
+                            es.s = st;
+                            const int r2 = elim_run(es);
+                            return r2 ? r2 : elim_gather(es, rank);
+                        });
 }
 
 int gf2_mul(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64_t *B, int64_t sb, int64_t m,

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+
 #include "../../include/gf2.h"
 
 typedef unsigned long long u64;
@@ -157,6 +159,26 @@ struct EventSet {
         return GF2_OK;
     }
 };
+
+// Replay of repeated calls from CUDA graphs (gf2_graph.cu): the key holds every
+// argument that the launches depend on; body enqueues the call on its stream.
+// Graph replay of repeated calls (gf2_graph.cu). The key is everything a call's
+// launches depend on; the stream is not part of it (graphs are captured on a
+// private stream and launched on the caller's). body(st) enqueues the call's
+// work on st.
+struct CallKey {
+    int op, device, tile_words, grid;
+    const void *A;
+    int64_t m, n, stride;
+    const void *P, *Q, *rank, *pivots, *work;
+    size_t work_bytes;
+};
+int run_replayed(const CallKey &key, cudaStream_t s, const std::function<int(cudaStream_t)> &body);
+bool capturing_on_this_thread();  // side_stream() then hands out the private capture side stream
+// private streams of the current device for captures: origin and side (gf2_pls.cu)
+int capture_streams(cudaStream_t *origin, cudaStream_t *side);
+bool prof_timing_on();  // launch timing (events around launches) is enabled
+long long launches_by_thread();  // all launches this thread has made (profiling on or off)
 
 // argument checks and the internal per-device workspace (gf2_api.cu)
 int get_work(void *&work, size_t &work_bytes, size_t need);  // caller's work if given, else the internal one

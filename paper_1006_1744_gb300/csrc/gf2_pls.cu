@@ -1430,15 +1430,17 @@ int identity_fill(int64_t *P, int64_t m, int64_t *Q, int64_t n, int64_t *rank, c
     return note_cuda(cudaGetLastError());
 }
 
-// Side streams for the look-ahead: a few per device, created on first use.
+// Side streams for the look-ahead, created on first use. Per device: four
+// handed out round robin, plus the origin and side stream of graph captures
+// (used by one capture at a time).
 struct SideStreams {
     std::mutex mu;
-    cudaStream_t s[64][4] = {};
+    cudaStream_t s[64][6] = {};
     unsigned next[64] = {};
 };
 static SideStreams g_side;
 
-int side_stream(cudaStream_t *out)
+static int device_streams(cudaStream_t **out)
 {
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
@@ -1446,11 +1448,38 @@ int side_stream(cudaStream_t *out)
         return note_cuda(err);
     if (dev < 0 || dev >= 64)
         return GF2_EINVAL;
+    if (!g_side.s[dev][0])  // all at once, so that no later call creates one
+        for (int k = 0; k < 6; ++k)
+            if ((err = cudaStreamCreateWithFlags(&g_side.s[dev][k], cudaStreamNonBlocking)) != cudaSuccess)
+                return note_cuda(err);
+    *out = g_side.s[dev];
+    return GF2_OK;
+}
+
+int side_stream(cudaStream_t *out)
+{
     std::lock_guard<std::mutex> lock(g_side.mu);
-    const unsigned k = g_side.next[dev]++ & 3u;
-    if (!g_side.s[dev][k] && (err = cudaStreamCreateWithFlags(&g_side.s[dev][k], cudaStreamNonBlocking)) != cudaSuccess)
-        return note_cuda(err);
-    *out = g_side.s[dev][k];
+    cudaStream_t *ds = nullptr;
+    if (const int rc = device_streams(&ds))
+        return rc;
+    if (capturing_on_this_thread()) {
+        *out = ds[5];
+        return GF2_OK;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    *out = ds[g_side.next[dev]++ & 3u];
+    return GF2_OK;
+}
+
+int capture_streams(cudaStream_t *origin, cudaStream_t *side)
+{
+    std::lock_guard<std::mutex> lock(g_side.mu);
+    cudaStream_t *ds = nullptr;
+    if (const int rc = device_streams(&ds))
+        return rc;
+    *origin = ds[4];
+    *side = ds[5];
     return GF2_OK;
 }
 

@@ -44,10 +44,17 @@ int take_event(Prof &p)
 }
 }  // namespace
 
+bool prof_timing_on() { return prof().flags.load(std::memory_order_relaxed) & 2; }
+
+// every launch of this thread, counted or not (lets a replayed graph report its launches)
+static thread_local long long t_all_launches = 0;
+long long launches_by_thread() { return t_all_launches; }
+
 void prof_launched(int count)
 {
+    t_all_launches += count;
     Prof &p = prof();
-    if (p.flags.load(std::memory_order_relaxed) & 1)
+    if ((p.flags.load(std::memory_order_relaxed) & 1) && !capturing_on_this_thread())  // a capture runs nothing
         p.launches.fetch_add(count, std::memory_order_relaxed);
 }
 

@@ -19,7 +19,8 @@ namespace {
 // columns (-> B row i, positions Q[i]-i .., the positions before are zero).
 __global__ void k_rref_compact(const uint64_t *__restrict__ S, int64_t stride, const int64_t *__restrict__ Q,
                                const u64 *__restrict__ pmask, const PanelState *__restrict__ st,
-                               uint64_t *__restrict__ U1, u64 *__restrict__ Bc, int64_t sb, int n, int W)
+                               uint64_t *__restrict__ U1, int64_t ustride, u64 *__restrict__ Bc, int64_t sb, int n,
+                               int W)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int r = st->r_next;
@@ -28,7 +29,7 @@ __global__ void k_rref_compact(const uint64_t *__restrict__ S, int64_t stride, c
     const int nn = n - r;
     const int64_t q = Q[i];
     const uint64_t *row = S + (int64_t)i * stride;
-    uint64_t *urow = U1 + (int64_t)i * stride;
+    uint64_t *urow = U1 + (int64_t)i * ustride;
     u64 *brow = Bc + (int64_t)i * sb;
     // U1 stream from position i, B stream from position q - i
     int64_t up = i, bp = q - i;
@@ -336,7 +337,8 @@ int rref_finish(const Elim &e, const ElimLayout &L, char *work, int64_t *rank, i
         return note_cuda(err);
     k_pmask2<<<64, 256, 0, e.s>>>(e.Q, e.stf, e.pmask);
     const int rmax = m < n ? m : n;
-    k_rref_compact<<<(rmax + 127) / 128, 128, 0, e.s>>>(e.out, e.ostride, e.Q, e.pmask, e.stf, e.A, Bc, sb, n, W);
+    k_rref_compact<<<(rmax + 127) / 128, 128, 0, e.s>>>(e.out, e.ostride, e.Q, e.pmask, e.stf, e.A, e.stride, Bc, sb, n,
+                                                          W);
     const int nblk = (rmax + 63) / 64;
     k_diag_inv<<<(nblk + 3) / 4, 128, 0, e.s>>>(e.A, e.stride, e.stf, Dinv, nblk);
     prof_launched(3);

@@ -62,6 +62,8 @@ SYMBOLS = {
     "gf2_autotune": (_int, [_int, _i64, _i64, ctypes.c_double, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_double), _vp]),
     "gf2_sync_status": (_int, [_vp]),
     "gf2_diag_wait_timeout": (_int, [ctypes.c_uint64, _vp]),
+    "gf2_replay_enable": (None, [_int]),
+    "gf2_replay_stats": (None, [ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
     "gf2_prof_enable": (None, [_int]),
     "gf2_prof_reset": (None, []),
     "gf2_prof_launches": (ctypes.c_longlong, []),
@@ -69,6 +71,19 @@ SYMBOLS = {
 }
 
 PROF_SWEEP, PROF_PIVOT, PROF_RREF, PROF_MUL = 0, 1, 2, 3
+
+
+def replay_enable(on: bool) -> None:
+    """Switch graph replay of repeated pls/rref/rank calls on or off (process-wide)."""
+    lib().gf2_replay_enable(1 if on else 0)
+
+
+def replay_stats():
+    """(graphs captured, calls replayed) since the process started."""
+    c = ctypes.c_longlong(0)
+    r = ctypes.c_longlong(0)
+    lib().gf2_replay_stats(ctypes.byref(c), ctypes.byref(r))
+    return int(c.value), int(r.value)
 
 
 def prof_enable(flags: int) -> None:

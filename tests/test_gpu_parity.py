@@ -97,6 +97,60 @@ def test_pls_empty(g):
         assert (P.cpu().numpy() == np.arange(m)).all() and (Q.cpu().numpy() == np.arange(n)).all()
 
 
+def test_repeated_calls_replay_with_new_contents(g):
+    """The same argument list called again is replayed from a captured graph;
+    every call, direct or replayed, must see the buffers' current contents."""
+    g.replay_enable(True)
+    m, n = 700, 900
+    D = torch.empty((m, 32), dtype=torch.int64, device="cuda")  # stride 32 words > 15 used
+    P = torch.empty(m, dtype=torch.int64, device="cuda")
+    Q = torch.empty(n, dtype=torch.int64, device="cuda")
+    rk = torch.empty(1, dtype=torch.int64, device="cuda")
+    piv = torch.empty(n, dtype=torch.int64, device="cuda")
+    side = torch.cuda.Stream()
+    c0, r0 = g.replay_stats()
+    for it in range(6):
+        kind = KINDS[it % len(KINDS)]
+        A = make(kind, m, n, 900 + it)
+        W = S.words_per_row(n)
+        # PLS on the default stream
+        D.zero_()
+        D[:, :W].copy_(torch.from_numpy(np.ascontiguousarray(A[:, :W]).view(np.int64)))
+        g.pls(D, n, P=P, Q=Q, rank=rk)
+        torch.cuda.synchronize()
+        R, Po, Qo, r = oracle.pls(A, m, n)
+        assert int(rk.item()) == r and (P.cpu().numpy() == Po).all() and (Q.cpu().numpy() == Qo).all()
+        assert (host(D)[:, :W] == R[:, :W]).all()
+        # rank (input untouched) and RREF on another stream
+        D[:, :W].copy_(torch.from_numpy(np.ascontiguousarray(A[:, :W]).view(np.int64)))
+        torch.cuda.synchronize()
+        with torch.cuda.stream(side):
+            g.rank(D, n, rank=rk, stream=side)
+        side.synchronize()
+        assert int(rk.item()) == r
+        with torch.cuda.stream(side):
+            g.rref(D, n, rank=rk, pivots=piv, stream=side)
+        side.synchronize()
+        Rr, pv, rr = oracle.rref(A, m, n)
+        assert int(rk.item()) == rr and (piv.cpu().numpy()[:rr] == pv).all()
+        assert (host(D)[:, :W] == Rr[:, :W]).all()
+    c1, r1 = g.replay_stats()
+    assert c1 - c0 >= 3 and r1 - r0 >= 3 * 3, (c1 - c0, r1 - r0)
+
+
+def test_replay_off_matches(g):
+    m, n = 300, 500
+    A = S.dense(m, n, 77)
+    g.replay_enable(False)
+    try:
+        c0, r0 = g.replay_stats()
+        for _ in range(3):
+            check_pls(g, A, m, n)
+        assert g.replay_stats() == (c0, r0)
+    finally:
+        g.replay_enable(True)
+
+
 def check_rref(g, A, m, n):
     R, piv, r = oracle.rref(A, m, n)
     D = dev(A)
@@ -121,6 +175,26 @@ def test_rref_parity_wide_rank_deficient(g):
     for (m, n) in [(300, 2000), (1000, 1500), (2100, 700)]:
         for kind in ("dense", "lowrank", "echelon", "sparse01"):
             check_rref(g, make(kind, m, n, 7 * m + n), m, n)
+
+
+def test_rref_and_rank_parity_wide_stride(g):
+    """Row pitch above the minimum: the result must land in the caller's rows."""
+    for (m, n, stride) in [(700, 900, 32), (300, 500, 48), (129, 64, 32)]:
+        for kind in ("dense", "lowrank"):
+            A = make(kind, m, n, 3 * m + stride)
+            W = S.words_per_row(n)
+            Aw = np.zeros((m, stride), dtype=np.uint64)
+            Aw[:, :W] = A[:, :W]
+            Aw[:, W:] = np.uint64(0x5A5A5A5A5A5A5A5A)  # words past the row must stay untouched
+            D = dev(Aw)
+            assert int(g.rank(D, n).item()) == oracle.rank(A, m, n)
+            R, piv, r = oracle.rref(A, m, n)
+            rd, pd = g.rref(D, n)
+            torch.cuda.synchronize()
+            assert int(rd.item()) == r and (pd.cpu().numpy()[:r] == piv).all()
+            got = host(D)
+            assert (got[:, :W] == R[:, :W]).all()
+            assert (got[:, W:] == np.uint64(0x5A5A5A5A5A5A5A5A)).all()
 
 
 def test_rank_parity_and_input_untouched(g):
