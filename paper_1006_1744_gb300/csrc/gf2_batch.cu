@@ -121,6 +121,9 @@ int check_items(const gf2_batch_item *items, int64_t count)
     return GF2_OK;
 }
 
+int batched_run(const gf2_batch_item *items, int64_t count, int64_t *ranks, char *w, const BatchLayout &L, int tw,
+                cudaStream_t s);
+
 }  // namespace
 
 extern "C" {
@@ -142,12 +145,34 @@ int gf2_pls_batched(const gf2_batch_item *items, int64_t count, int64_t *ranks, 
         return GF2_OK;
     if (!ranks)
         return GF2_EINVAL;
-    cudaStream_t s = (cudaStream_t)stream;
     const BatchLayout L = batch_layout(items, count);
     if ((rc = gf2::get_work(work, work_bytes, L.total)))
         return rc;
-    char *w = (char *)work;
     const int tw = (opts && opts->tile_words) ? opts->tile_words : 16;
+    // a repeated call (same items, ranks, workspace, options) replays a captured graph
+    gf2::CallKey key;
+    std::memset(&key, 0, sizeof(key));
+    cudaGetDevice(&key.device);
+    key.op = -GF2_OP_PLS;
+    key.tile_words = tw;
+    key.m = count;
+    key.rank = ranks;
+    key.work = work;
+    key.work_bytes = work_bytes;
+    return gf2::run_replayed(
+        key, (cudaStream_t)stream,
+        [&](cudaStream_t s) { return batched_run(items, count, ranks, (char *)work, L, tw, s); }, items,
+        (size_t)count * sizeof(gf2_batch_item), L.mats);
+}
+
+}  // extern "C"
+
+namespace {
+
+int batched_run(const gf2_batch_item *items, int64_t count, int64_t *ranks, char *w, const BatchLayout &L, int tw,
+                cudaStream_t s)
+{
+    int rc = GF2_OK;
 
     // host image of descriptors + plan, uploaded in one copy
     std::vector<char> img(L.mats);
@@ -216,8 +241,13 @@ int gf2_pls_batched(const gf2_batch_item *items, int64_t count, int64_t *ranks, 
         io += nact;
         po += nact + 1;
     }
-    if ((rc = upload(w, img.data(), L.mats, s)))
+    if (void *stage = gf2::capture_stage()) {  // captured: the graph's own buffer, read on every replay
+        std::memcpy(stage, img.data(), L.mats);
+        if ((rc = gf2::note_cuda(cudaMemcpyAsync(w, stage, L.mats, cudaMemcpyHostToDevice, s))))
+            return rc;
+    } else if ((rc = upload(w, img.data(), L.mats, s))) {
         return rc;
+    }
     const gf2::ElimDesc *dD = reinterpret_cast<const gf2::ElimDesc *>(w + L.descs);
     const int *dIdx = reinterpret_cast<const int *>(w + L.idx);
     const int *dPre = reinterpret_cast<const int *>(w + L.pre);
@@ -258,4 +288,4 @@ int gf2_pls_batched(const gf2_batch_item *items, int64_t count, int64_t *ranks, 
     return GF2_OK;
 }
 
-}  // extern "C"
+}  // namespace

@@ -173,8 +173,14 @@ struct CallKey {
     const void *P, *Q, *rank, *pivots, *work;
     size_t work_bytes;
 };
-int run_replayed(const CallKey &key, cudaStream_t s, const std::function<int(cudaStream_t)> &body);
+// extra (nullable): further bytes the launches depend on (compared bytewise, e.g.
+// a batch's item list); stage_bytes: size of a pinned host buffer the graph owns,
+// which body reaches through capture_stage() while it is being captured (host
+// data that the graph copies to the device, unchanged for every replay).
+int run_replayed(const CallKey &key, cudaStream_t s, const std::function<int(cudaStream_t)> &body,
+                 const void *extra = nullptr, size_t extra_bytes = 0, size_t stage_bytes = 0);
 bool capturing_on_this_thread();  // side_stream() then hands out the private capture side stream
+void *capture_stage();            // the capture's pinned buffer (nullptr outside a capture)
 // private streams of the current device for captures: origin and side (gf2_pls.cu)
 int capture_streams(cudaStream_t *origin, cudaStream_t *side);
 bool prof_timing_on();  // launch timing (events around launches) is enabled

@@ -177,14 +177,18 @@ __device__ bool pivot_fast(int r, int m, int nwin, int nbits, int &t_out, u64 &J
     const bool all_rows = (m - r) <= WIN;
     int t = 0, j = 0;
     u64 J = 0;
+    // bit j of each row, kept one step ahead: after a pivot it follows from the row's old
+    // bit j + 1 and one bit of the pivot row, so the 64-bit XOR stays off the chain
+    bool cb[NSLOT];
+#pragma unroll
+    for (int k = 0; k < NSLOT; ++k)
+        cb[k] = row[k] & 1ull;
     while (t < 64 && j < nbits && t < nwin) {
-        const int jw = j >> 5, jb = j & 31;
         bool cand[NSLOT];
         int key = INT_MAX;
 #pragma unroll
         for (int k = 0; k < NSLOT; ++k) {
-            const unsigned h = jw ? (unsigned)(row[k] >> 32) : (unsigned)row[k];
-            cand[k] = act[k] && ((h >> jb) & 1u);
+            cand[k] = act[k] && cb[k];
             key = cand[k] ? min(key, (pos[k] << 7) | (k << 5) | lane) : key;
         }
         // first candidate in the current row order
@@ -193,6 +197,9 @@ __device__ bool pivot_fast(int r, int m, int nwin, int nbits, int &t_out, u64 &J
             if (!all_rows)
                 return false;  // a candidate may sit past the window
             ++j;               // zero column among all remaining rows
+#pragma unroll
+            for (int k = 0; k < NSLOT; ++k)
+                cb[k] = (row[k] >> (j & 63)) & 1ull;
             continue;
         }
         const int p = best >> 7, slot = (best >> 5) & 3, plane = best & 31;
@@ -212,11 +219,16 @@ __device__ bool pivot_fast(int r, int m, int nwin, int nbits, int &t_out, u64 &J
         }
         // swap positions t and p: the pivot takes t (and leaves the candidates), the row
         // at t takes p; rows below with a 1 in column j get the pivot row right of j
-        const u64 pm = prow & ~lowmask(j + 1);
+        const u64 pm = prow & (~1ull << j);
+        const int j1 = (j + 1) & 63;
+        const bool pb1 = (prow >> j1) & 1ull;
 #pragma unroll
         for (int k = 0; k < NSLOT; ++k) {
             const bool isp = lane == plane && k == slot;
-            row[k] ^= (cand[k] && !isp) ? pm : 0ull;
+            const bool x = cand[k] && !isp;
+            const bool ob1 = (row[k] >> j1) & 1ull;
+            row[k] ^= x ? pm : 0ull;
+            cb[k] = ob1 ^ (x && pb1);
             pos[k] = isp ? t : (pos[k] == t ? p : pos[k]);
             act[k] = act[k] && !isp;
         }
@@ -665,13 +677,29 @@ __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int6
         const bool isU = warp < 2;
         if (!isU || sFast) {
             const int col = lane + 32 * (warp & 1);
-            const u64 own = 1ull << col;
-            u64 X = 0, bit = isU ? (t > 0 ? 1ull << (t - 1) : 0ull) : 1ull;
-            for (int i = 0; i < t; ++i) {
-                const u64 a = (isU ? S.sVw[t - 1 - i] : S.sXl[i]) & X;
-                const bool par = __popc((unsigned)a ^ (unsigned)(a >> 32)) & 1;
-                X |= (par ? bit : 0ull) ^ (own & bit);
-                bit = isU ? bit >> 1 : bit << 1;
+            // four rows per step: their parities against the bits found so far are
+            // independent; a row selecting an earlier row of the same step is resolved after
+            const u64 *sel = isU ? S.sVw : S.sXl;
+            u64 X = 0;
+            for (int i0 = 0; i0 < t; i0 += 4) {
+                int rr[4], bb[4];
+                u64 sv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool ok = i0 + u < t;
+                    rr[u] = ok ? (isU ? t - 1 - i0 - u : i0 + u) : 0;
+                    sv[u] = ok ? sel[rr[u]] : 0ull;
+                    const u64 a = sv[u] & X;
+                    bb[u] = ok ? ((__popc((unsigned)a ^ (unsigned)(a >> 32)) & 1) ^ (int)(col == rr[u])) : 0;
+                }
+#pragma unroll
+                for (int u = 1; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < u; ++v)
+                        bb[u] ^= (int)((sv[u] >> rr[v]) & 1ull) & bb[v];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    X |= (u64)bb[u] << rr[u];
             }
             // 32 columns x 64 rows -> the warp's 32-bit half of every row
             unsigned *dst = reinterpret_cast<unsigned *>(isU ? S.sUi : S.sLi);
@@ -688,11 +716,16 @@ __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int6
     // columns. Two threads per row of M, each over half of the inner index.
     {
         const int row = tid >> 1, half = tid & 1;
-        const u64 ua = row < t ? S.sUi[row] : 0ull;
-        u64 ma = 0;
-        const int kend = min(t, 32 * half + 32);
-        for (int k = 32 * half; k < kend; ++k)
-            ma ^= ((ua >> k) & 1ull) ? S.sLi[k] : 0ull;
+        const u64 ua = row < t ? S.sUi[row] : 0ull;  // no bits at t and above
+        u64 acc[4] = {0ull, 0ull, 0ull, 0ull};        // four independent XOR chains
+#pragma unroll
+        for (int k0 = 0; k0 < 32; k0 += 4)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = 32 * half + k0 + u;
+                acc[u] ^= ((ua >> k) & 1ull) ? S.sLi[k] : 0ull;
+            }
+        u64 ma = (acc[0] ^ acc[1]) ^ (acc[2] ^ acc[3]);
         ma ^= __shfl_xor_sync(GF2_FULL, ma, 1);
         if (half == 0 && row < t) {
             sXp[S.sPcol[row]] = ma;

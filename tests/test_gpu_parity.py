@@ -394,6 +394,38 @@ def test_pls_batched_many_small_and_user_workspace(g):
             assert (host(ds[i])[:, :S.words_per_row(n)] == R[:, :S.words_per_row(n)]).all()
 
 
+def test_pls_batched_replayed_with_new_contents(g):
+    """The same batch (buffers, ranks, workspace) called again is replayed from a
+    captured graph, plan upload included; each call sees the current contents."""
+    g.replay_enable(True)
+    rng = np.random.default_rng(33)
+    shapes = [(int(rng.integers(1, 400)), int(rng.integers(1, 500))) for _ in range(40)]
+    mats = [torch.empty((m, S.default_stride(n)), dtype=torch.int64, device="cuda") for (m, n) in shapes]
+    ns = [n for (_, n) in shapes]
+    Ps = [torch.empty(m, dtype=torch.int64, device="cuda") for (m, _) in shapes]
+    Qs = [torch.empty(n, dtype=torch.int64, device="cuda") for (_, n) in shapes]
+    ranks = torch.empty(len(shapes), dtype=torch.int64, device="cuda")
+    work = torch.empty(g.pls_batched_workspace_bytes([(m, n, S.default_stride(n)) for (m, n) in shapes]) // 8 + 64,
+                       dtype=torch.int64, device="cuda")
+    c0, r0 = g.replay_stats()
+    kinds = ["dense", "sparse01", "lowrank", "echelon"]
+    for it in range(5):
+        hosts = [make(kinds[(i + it) % 4], m, n, 100 * it + i) for i, (m, n) in enumerate(shapes)]
+        for D, A in zip(mats, hosts):
+            D.copy_(torch.from_numpy(np.ascontiguousarray(A).view(np.int64)))
+        g.pls_batched(mats, ns, Ps=Ps, Qs=Qs, ranks=ranks, work=work)
+        torch.cuda.synchronize()
+        rk = ranks.cpu().numpy()
+        for i, ((m, n), A) in enumerate(zip(shapes, hosts)):
+            R, P, Q, r = oracle.pls(A, m, n)
+            assert rk[i] == r, (it, i)
+            assert (Ps[i].cpu().numpy() == P[:m]).all() and (Qs[i].cpu().numpy() == Q[:n]).all(), (it, i)
+            W = S.words_per_row(n)
+            assert (host(mats[i])[:, :W] == R[:, :W]).all(), (it, i)
+    c1, r1 = g.replay_stats()
+    assert c1 - c0 == 1 and r1 - r0 == 3, (c1 - c0, r1 - r0)
+
+
 def test_autotune_choices_are_exact_and_cached(g):
     """The autotuner only picks among settings that change no result: PLS with its
     choice matches the oracle, and a second call returns the cached choice."""
