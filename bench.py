@@ -596,6 +596,17 @@ def main():
                 "avg_launch_us": sweep_ms * 1e3 / max(sweep_n, 1),
                 "note": "16384^2 packed is 32 MB and stays in the 129 MB L2 within a step"}
 
+    # the pivot search is one warp's dependent chain, not a bandwidth kernel: report it
+    # against the floor of that chain, one warp min-reduction (26 cycles) plus one 64-bit
+    # shuffle (38 cycles) per pivot at the SM clock (latencies measured on GB300 with a
+    # dependent-chain probe), 64 pivots per panel
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    pivot_us = pivot_ms * 1e3 / max(pivot_n, 1)
+    floor_us = 64 * (26 + 38) / sm_mhz
+    pivot_chain = {"kernel": "k_pivot (panel pivot search: PlsSubmatrix)", "bound": "latency",
+                   "avg_launch_us": pivot_us, "chain_floor_us": floor_us, "frac": floor_us / pivot_us if pivot_us else 0.0,
+                   "note": "1 CTA; the elimination chain of 64 pivots, plus window formation and the inverses"}
+
     # ---- end to end: host buffers, copies inside the timed region ---------------------
     e2e = None
     if not args.no_e2e:
@@ -659,7 +670,7 @@ def main():
         "pls_s": pls_ms / 1e3, "rref_s": rref_ms / 1e3, "rank": rank_val,
         "bitops_per_s": effective_bitops(m, n, rank_val) / (pls_ms / 1e3),
         "wall_s_timed_region": wall,
-        "roofline": roofline,
+        "roofline": roofline, "pivot_chain": pivot_chain,
         "kernel_time_shares": {k: v / tot for k, v in shares.items()}, "dominant_kernel": dominant,
         "kernel_launches": {"sweep": sweep_n, "pivot": pivot_n, "rref_block": rref_blk_n},
         "gpu_launches": launches,

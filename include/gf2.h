@@ -80,7 +80,7 @@ extern "C" {
 typedef struct gf2_opts {
     int k;              /* bits per Gray-code table (Sec. 3.1); only 8 is built, 0 = 8 */
     int tile_words;     /* column tile of a table sweep, in words: 0 (default), 4, 8 or 16 */
-    int grid_ctas;      /* CTAs of a table sweep; 0 = one per SM */
+    int grid_ctas;      /* CTAs of a table sweep; 0 = one per SM but one (left to the overlapping pivot search) */
     int product;        /* GF2_PRODUCT_*; used by gf2_mul */
     int64_t cutoff_cols;/* recursive PLS: MMPF base case at or below this many columns (Sec. 6); 0 = MMPF only */
     int reserved[8];    /* must be zero */

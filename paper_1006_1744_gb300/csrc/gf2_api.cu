@@ -177,7 +177,10 @@ static Elim make_elim(uint64_t *A, int64_t m, int64_t n, int64_t stride, char *w
     e.Q = Q;
     e.s = s;
     e.tile_words = (o && o->tile_words) ? o->tile_words : 16;
-    e.grid = (o && o->grid_ctas) ? o->grid_ctas : sm_count();
+    // default: one CTA per SM but one, so the look-ahead pivot search (which cannot share an
+    // SM with a 1024-thread sweep CTA) never holds back a CTA of the sweep it overlaps
+    const int nsm = sm_count();
+    e.grid = (o && o->grid_ctas) ? o->grid_ctas : (nsm > 1 ? nsm - 1 : 1);
     return e;
 }
 
