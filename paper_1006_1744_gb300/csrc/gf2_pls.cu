@@ -777,10 +777,16 @@ __device__ __forceinline__ void apply_order(int *__restrict__ perm, const PanelS
 
 __global__ void k_apply_order(int *__restrict__ perm, const PanelState *__restrict__ st) { apply_order(perm, st); }
 
+// Launched as a programmatic dependent of the previous panel's search (same stream):
+// it may be scheduled while that search still runs, lets the next one be scheduled in
+// turn, and waits on the device until its predecessor has completed and its writes
+// are visible. Without the launch attribute both instructions are no-ops.
 __global__ void __launch_bounds__(PIVOT_THREADS, 1)
 k_pivot(const uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_prev, int *__restrict__ perm,
         const PanelState *__restrict__ st_prev, PanelState *st, int64_t *P, int64_t *Q, int m, int b, int nbits)
 {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     pivot_panel(A, stride, side_prev, perm, st_prev, st, P, Q, m, b, nbits);
 }
 
@@ -1542,11 +1548,25 @@ int elim_run(const Elim &e)
         if (b >= 2 && (rc = note_cuda(cudaStreamWaitEvent(e.s, ev_rest[b & 1], 0))))
             return rc;
         const int tok = prof_begin(e.s);
-        k_pivot<<<1, PIVOT_THREADS, 0, e.s>>>(e.A, e.stride, prev, e.perm, e.st + ((b + 1) & 1), stb, e.P, e.Q, m, b,
-                                              nbits);
+        {
+            // the previous panel's search is the preceding kernel on s: a programmatic
+            // dependency lets this launch be scheduled before it completes (k_pivot waits)
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(1);
+            cfg.blockDim = dim3(PIVOT_THREADS);
+            cfg.stream = e.s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = b > 0 ? 1 : 0;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            const PanelState *stp = e.st + ((b + 1) & 1);
+            rc = note_cuda(cudaLaunchKernelEx(&cfg, k_pivot, (const uint64_t *)e.A, e.stride, prev, e.perm, stp, stb,
+                                              e.P, e.Q, m, b, nbits));
+        }
         prof_end(e.s, GF2_PROF_PIVOT, tok);
         prof_launched(1);
-        if ((rc = note_cuda(cudaGetLastError())) || (rc = note_cuda(cudaEventRecord(ev_piv, e.s))) ||
+        if (rc || (rc = note_cuda(cudaGetLastError())) || (rc = note_cuda(cudaEventRecord(ev_piv, e.s))) ||
             (rc = note_cuda(cudaStreamWaitEvent(t, ev_piv, 0))))
             return rc;
         rc = e.tile_words == 4   ? launch_sweep<4, 1, 512, 2>(e, b, t)
