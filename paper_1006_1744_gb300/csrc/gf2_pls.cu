@@ -804,9 +804,9 @@ k_pivot(const uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ 
 // from A while the sweep runs. The CTA holding word b+1 also stores it in the
 // next panel's side buffer.
 //
-// Work: column tiles of TW words (from the even word <= b) x row chunks; a CTA
-// keeps its tables while consecutive work items share a tile, and keeps RPT
-// rows per thread in flight.
+// Work: column tiles of TW words (from the even word <= b) x blocks of rows; each
+// CTA takes an equal contiguous run of that tile-major sequence, builds a tile's
+// tables once per tile it meets, and keeps RPT rows per thread in flight.
 // ---------------------------------------------------------------------------
 // physical row at trailing position p of the panel that st describes: its
 // window order, its swaps past the window, else perm (which the next panel's
@@ -918,13 +918,12 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
     const int wstart = b & ~1;
     const int tiles = (W - wstart + TW - 1) / TW;
     constexpr int PASS = RPP * RPT;  // rows per pass of the CTA
-    int chunks = ncta / tiles;
-    if (chunks < 1)
-        chunks = 1;
-    int R = (M + chunks - 1) / chunks;
-    R = (R + PASS - 1) / PASS * PASS;
-    chunks = (M + R - 1) / R;
-    const int items = tiles * chunks;
+    // Work: the tiles x (blocks of PASS rows) in tile-major order, cut into ncta
+    // contiguous runs of equal length (to one block): every CTA is busy and a run
+    // spans at most a few tiles, so the tables are rebuilt at most that often
+    const int nblk = (M + PASS - 1) / PASS;
+    const long long T = (long long)tiles * nblk;
+    const long long q_lo = T * cta / ncta, q_hi = T * (cta + 1) / ncta;
     const int ng = (kbar + 7) >> 3;
 
     if (tid < 64)
@@ -949,8 +948,11 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
     // lanes of one row form an aligned group of TPR lanes
     const unsigned gmask = (TPR == 32 ? GF2_FULL : ((1u << TPR) - 1u) << (lane & ~(TPR - 1)));
     int cur_tile = -1;
-    for (int item = cta; item < items; item += ncta) {
-        const int tile = item / chunks, chunk = item % chunks;
+    for (long long q = q_lo; q < q_hi;) {
+        const int tile = (int)(q / nblk);
+        const long long q_end = min(q_hi, (long long)(tile + 1) * nblk);
+        const int blk0 = (int)(q - (long long)tile * nblk), blk1 = (int)(q_end - (long long)tile * nblk);
+        q = q_end;
         const int wbase = wstart + tile * TW;
         if (tile != cur_tile) {
             __syncthreads();
@@ -989,8 +991,8 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
             __syncthreads();
             cur_tile = tile;
         }
-        const int p_begin = r + chunk * R;
-        const int p_end = min(m, p_begin + R);
+        const int p_begin = r + blk0 * PASS;
+        const int p_end = min(m, r + blk1 * PASS);
         const int w0 = wbase + 2 * sub;
         const bool two = w0 + 1 < W;
         const bool wact = w0 < W;
