@@ -915,7 +915,10 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
             atomicExch(const_cast<int *>(&st->nz), 1);
         return;
     }
-    const int wstart = b & ~1;
+    // tiles start on a 64-byte boundary (32 bytes for 4-word tiles), so a row-tile's
+    // store covers whole DRAM atoms; words left of b - 1 in the first tile are skipped
+    constexpr int WAL = TW < 8 ? TW : 8;
+    const int wstart = b & ~(WAL - 1);
     const int tiles = (W - wstart + TW - 1) / TW;
     constexpr int PASS = RPP * RPT;  // rows per pass of the CTA
     // Work: the tiles x (blocks of PASS rows) in tile-major order, cut into ncta
@@ -995,7 +998,7 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
         const int p_end = min(m, r + blk1 * PASS);
         const int w0 = wbase + 2 * sub;
         const bool two = w0 + 1 < W;
-        const bool wact = w0 < W;
+        const bool wact = w0 < W && w0 + 1 >= b;  // both words left of the panel: untouched
         // software pipeline over passes: the physical rows of the pass after next and
         // the words of the next pass are in flight while this pass is computed
         int ph[RPT], phB[RPT], phC[RPT];
