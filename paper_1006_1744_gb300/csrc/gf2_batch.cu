@@ -210,7 +210,7 @@ int batched_run(const gf2_batch_item *items, int64_t count, int64_t *ranks, char
     for (int b = 0; b < L.Wmax; ++b) {
         step_idx_off[b] = (int)io;
         step_pre_off[b] = (int)po;
-        const int wstart = b & ~(tw < 8 ? tw - 1 : 7);  // the sweep's first tile (64-byte aligned)
+        const int wstart = b & ~(tw - 1);  // the sweep's first tile
         double total_work = 0;
         int nact = 0;
         work_est.clear();

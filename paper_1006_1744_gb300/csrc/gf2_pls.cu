@@ -917,7 +917,7 @@ __device__ __forceinline__ void sweep_panel(uint64_t *__restrict__ A, int64_t st
     }
     // tiles start on a 64-byte boundary (32 bytes for 4-word tiles), so a row-tile's
     // store covers whole DRAM atoms; words left of b - 1 in the first tile are skipped
-    constexpr int WAL = TW < 8 ? TW : 8;
+    constexpr int WAL = TW;
     const int wstart = b & ~(WAL - 1);
     const int tiles = (W - wstart + TW - 1) / TW;
     constexpr int PASS = RPP * RPT;  // rows per pass of the CTA
