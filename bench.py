@@ -228,6 +228,7 @@ def run_config3(args):
     """65536 x 65536 matrices (512 MB packed): dense Bernoulli(1/2), A = B.C with B 65536 x 32768 and
     C 32768 x 65536 (rank <= 32768), and Bernoulli(0.01); each through the panel elimination alone
     (MMPF) and the recursive PLS with the XOR-table and the tensor-core trailing product."""
+    import numpy as np
     import torch
     from paper_1006_1744_gb300 import build, gf2, synth, synth_gpu
     build.build()
@@ -264,8 +265,20 @@ def run_config3(args):
         results[variant] = {}
         for name, o in methods.items():
             rank = torch.empty(1, dtype=torch.int64, device=dev)
-            ms = _timed(lambda: gf2.pls(A, n, rank=rank, opts=o), steps, 1, pre=lambda: A.copy_(A0))
+            Qb = torch.empty(n, dtype=torch.int64, device=dev)
+            ms = _timed(lambda: gf2.pls(A, n, Q=Qb, rank=rank, opts=o), steps, 1, pre=lambda: A.copy_(A0))
             results[variant][name] = {"ms": ms, "rank": int(rank.item())}
+            if name == "mmpf":
+                # the panel sweeps' algorithmic bytes (read + write of every panel's trailing
+                # block) over the whole elimination's time: a lower bound on the sweeps' HBM rate
+                rv = int(rank.item())
+                W = (n + 63) // 64
+                rb = np.searchsorted(Qb[:rv].cpu().numpy(), 64 * np.arange(W))
+                byts = float(np.sum((n - rb).clip(min=0) * (W - np.arange(W)) * 16.0))
+                hbm, _ = peaks()
+                gbs = byts / (ms * 1e-3) / 1e9
+                results[variant][name].update({"sweep_algorithmic_GB": byts / 1e9, "sweep_GBps_over_elimination": gbs,
+                                               "hbm_frac": gbs / hbm})
         torch.cuda.empty_cache()
     gf2.prof_enable(0)
     clocks = sampler.stop()
@@ -461,7 +474,7 @@ def main():
                     help="2: the headline line (default); 3: 65536^2 matrices, MMPF vs recursive PLS with "
                          "XOR-table and tensor-core products; 4: batched PLS of 2048 matrices; 5: a stream of "
                          "requests with Poisson arrivals, batched as they arrive")
-    ap.add_argument("--requests", type=int, default=1024, help="config 5: requests per arrival rate")
+    ap.add_argument("--requests", type=int, default=4096, help="config 5: requests per arrival rate")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
