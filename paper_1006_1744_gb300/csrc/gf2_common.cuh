@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <functional>
 
 #include "../../include/gf2.h"
@@ -183,6 +184,21 @@ bool capturing_on_this_thread();  // side_stream() then hands out the private ca
 void *capture_stage();            // the capture's pinned buffer (nullptr outside a capture)
 // private streams of the current device for captures: origin and side (gf2_pls.cu)
 int capture_streams(cudaStream_t *origin, cudaStream_t *side);
+// Function attributes (the dynamic shared-memory limit) are per device: a launch site
+// keeps a mask of the devices it has set them on (setting twice is harmless).
+inline bool attr_needed(const std::atomic<unsigned long long> &devs)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+        return true;
+    return !((devs.load(std::memory_order_relaxed) >> dev) & 1ull);
+}
+inline void attr_done(std::atomic<unsigned long long> &devs)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64)
+        devs.fetch_or(1ull << dev, std::memory_order_relaxed);
+}
 bool prof_timing_on();  // launch timing (events around launches) is enabled
 long long launches_by_thread();  // all launches this thread has made (profiling on or off)
 

@@ -108,13 +108,13 @@ int mul_xor(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64
 {
     constexpr int TW = 8, RPT = 8;
     const size_t smem = (size_t)(8 * 256 * TW + 64 * TW) * sizeof(u64);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<unsigned long long> attr_devs{0};
+    if (attr_needed(attr_devs)) {
         int rc = note_cuda(
             cudaFuncSetAttribute(k_mul_xor<TW, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         if (rc)
             return rc;
-        attr_set = true;
+        attr_done(attr_devs);
     }
     (void)tile_words;
     const int W = (int)((n + 63) >> 6);

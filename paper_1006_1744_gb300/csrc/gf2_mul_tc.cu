@@ -376,12 +376,12 @@ int mul_tensor(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uin
             return note_cuda(cudaMemset2DAsync(C, (size_t)sc * 8, 0, (size_t)((n + 63) / 64) * 8, (size_t)m, s));
         return GF2_OK;
     }
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr_devs{0};
+    if (attr_needed(attr_devs)) {
         int rc = note_cuda(cudaFuncSetAttribute(k_mul_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
         if (rc)
             return rc;
-        attr = true;
+        attr_done(attr_devs);
     }
     int *status = status_word();
     if (!status)

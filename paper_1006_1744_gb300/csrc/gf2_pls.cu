@@ -1271,14 +1271,14 @@ constexpr size_t sweep_smem()
 template <int TW, int RPT, int NT, int MINB>
 int launch_sweep(const gf2::Elim &e, int b, cudaStream_t s)
 {
-    static bool attr_set = false;  // per process; the attribute is per function
+    static std::atomic<unsigned long long> attr_devs{0};
     constexpr size_t smem = sweep_smem<TW>();
-    if (!attr_set) {
+    if (gf2::attr_needed(attr_devs)) {
         cudaError_t err =
             cudaFuncSetAttribute(k_sweep<TW, RPT, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess)
             return gf2::note_cuda(err);
-        attr_set = true;
+        gf2::attr_done(attr_devs);
     }
     const u64 *cur = e.side + (size_t)(b & 1) * e.m;
     u64 *nxt = e.side + (size_t)((b + 1) & 1) * e.m;
@@ -1418,14 +1418,14 @@ template <int TW, int RPT, int NT, int MINB>
 static int launch_sweep_b(const ElimDesc *D, const int *idx, const int *pre, int nact, int total, int b,
                           cudaStream_t s)
 {
-    static bool attr_set = false;
+    static std::atomic<unsigned long long> attr_devs{0};
     constexpr size_t smem = sweep_smem<TW>();
-    if (!attr_set) {
+    if (attr_needed(attr_devs)) {
         cudaError_t err =
             cudaFuncSetAttribute(k_sweep_b<TW, RPT, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess)
             return note_cuda(err);
-        attr_set = true;
+        attr_done(attr_devs);
     }
     const int tok = prof_begin(s);
     k_sweep_b<TW, RPT, NT, MINB><<<total, NT, smem, s>>>(D, idx, pre, nact, b);

@@ -314,11 +314,11 @@ static int trsm_lower(const uint64_t *L, int64_t sl, uint64_t *B, int64_t sb, in
     if (rc)
         return rc;
     const size_t smem = (size_t)(2 * 8 * 256 * TWR + 2 * 64 * TWR + 64) * sizeof(u64);
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr_devs{0};
+    if (attr_needed(attr_devs)) {
         if ((rc = note_cuda(cudaFuncSetAttribute(k_trsm_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))))
             return rc;
-        attr = true;
+        attr_done(attr_devs);
     }
     uint64_t *X = w.scratch;
     const int64_t sx = w.scratch_stride;

@@ -348,15 +348,15 @@ int rref_finish(const Elim &e, const ElimLayout &L, char *work, int64_t *rank, i
     const int grid = sm_count();
     const size_t smem_g = (size_t)(G * 64 * TW1 + G * 64 * G + 8 * 256 * TW1 + 64 * TW1 + G * 64) * sizeof(u64);
     const size_t smem_b = (size_t)(G * 8 * 256 * TWG + G * 64 * TWG) * sizeof(u64);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<unsigned long long> attr_devs{0};
+    if (attr_needed(attr_devs)) {
         rc = note_cuda(cudaFuncSetAttribute(k_rref_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_g));
         if (!rc)
             rc = note_cuda(
                 cudaFuncSetAttribute(k_rref_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b));
         if (rc)
             return rc;
-        attr_set = true;
+        attr_done(attr_devs);
     }
     // B tiles of the group solve: ceil(NB / TW1) CTAs, NB <= W
     const int gtiles = (W + TW1 - 1) / TW1;
