@@ -692,11 +692,19 @@ __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int6
                     const u64 a = sv[u] & X;
                     bb[u] = ok ? ((__popc((unsigned)a ^ (unsigned)(a >> 32)) & 1) ^ (int)(col == rr[u])) : 0;
                 }
+                // the step's rows sit at base .. base + 3 (base < 0 only in U's last, partial
+                // step, whose missing rows select nothing): one shift per selector, then the
+                // in-step entries are constant-position bits
+                const int base = isU ? t - 4 - i0 : i0;
+                unsigned sl[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    sl[u] = base >= 0 ? (unsigned)(sv[u] >> base) : (unsigned)(sv[u] << -base);
 #pragma unroll
                 for (int u = 1; u < 4; ++u)
 #pragma unroll
                     for (int v = 0; v < u; ++v)
-                        bb[u] ^= (int)((sv[u] >> rr[v]) & 1ull) & bb[v];
+                        bb[u] ^= (int)((sl[u] >> (isU ? 3 - v : v)) & 1u) & bb[v];
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
                     X |= (u64)bb[u] << rr[u];
