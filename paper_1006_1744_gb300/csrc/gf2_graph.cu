@@ -47,15 +47,23 @@ bool same(const Entry &e, const gf2::CallKey &k, const void *extra, size_t extra
            (extra_bytes == 0 || std::memcmp(e.extra.data(), extra, extra_bytes) == 0);
 }
 
-// a dropped graph may still be running (or about to read its staging buffer)
+// a dropped graph may still be running (or about to read its staging buffer): wait
+// for its own device first
 void release(Entry &e)
 {
-    if (e.exec || e.stage)
+    if (e.exec || e.stage) {
+        int cur = 0;
+        const bool switched = cudaGetDevice(&cur) == cudaSuccess && cur != e.key.device &&
+                              cudaSetDevice(e.key.device) == cudaSuccess;
         cudaDeviceSynchronize();
-    if (e.exec)
-        cudaGraphExecDestroy(e.exec);
-    if (e.stage)
-        cudaFreeHost(e.stage);
+        if (e.exec)
+            cudaGraphExecDestroy(e.exec);
+        if (e.stage)
+            cudaFreeHost(e.stage);
+        if (switched)
+            cudaSetDevice(cur);
+        cudaGetLastError();
+    }
     e.exec = nullptr;
     e.stage = nullptr;
 }

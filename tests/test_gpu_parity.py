@@ -138,6 +138,39 @@ def test_repeated_calls_replay_with_new_contents(g):
     assert c1 - c0 >= 3 and r1 - r0 >= 3 * 3, (c1 - c0, r1 - r0)
 
 
+def test_replay_cache_eviction(g):
+    """More distinct argument lists than the graph cache holds (32): each is run,
+    captured and replayed, older graphs are dropped, and calls whose graph was
+    dropped start over; every result matches the oracle."""
+    g.replay_enable(True)
+    m, n = 96, 130
+    W = S.words_per_row(n)
+    bufs = [(torch.empty((m, S.default_stride(n)), dtype=torch.int64, device="cuda"),
+             torch.empty(m, dtype=torch.int64, device="cuda"), torch.empty(n, dtype=torch.int64, device="cuda"),
+             torch.empty(1, dtype=torch.int64, device="cuda")) for _ in range(40)]
+    work = g.new_workspace(g.OP_PLS, m, n)
+
+    def run(i, seed):
+        D, P, Q, rk = bufs[i]
+        A = make("dense" if seed % 2 else "lowrank", m, n, seed)
+        D.copy_(torch.from_numpy(np.ascontiguousarray(A).view(np.int64)))
+        g.pls(D, n, P=P, Q=Q, rank=rk, work=work)
+        torch.cuda.synchronize()
+        R, Po, Qo, r = oracle.pls(A, m, n)
+        assert int(rk.item()) == r and (P.cpu().numpy() == Po).all() and (Q.cpu().numpy() == Qo).all(), (i, seed)
+        assert (host(D)[:, :W] == R[:, :W]).all(), (i, seed)
+
+    c0, r0 = g.replay_stats()
+    for i in range(40):
+        for k in range(3):
+            run(i, 1000 * i + k)
+    for i in range(5):  # dropped long ago: direct, captured, replayed again
+        for k in range(3):
+            run(i, 7 + 1000 * i + k)
+    c1, r1 = g.replay_stats()
+    assert c1 - c0 == 45 and r1 - r0 == 45, (c1 - c0, r1 - r0)
+
+
 def test_replay_off_matches(g):
     m, n = 300, 500
     A = S.dense(m, n, 77)
