@@ -106,7 +106,7 @@ __global__ void k_diag_inv(const uint64_t *__restrict__ U1, int64_t stride, cons
 //   B_i += sum over the group's blocks q of U1[i, block q] . X_q,
 // with one Gray-code table per 8 pivots (G x 8 tables).
 constexpr int G = 8;     // blocks per group
-constexpr int TW1 = 2;   // words of B per CTA in the group solve
+constexpr int TW1 = 1;   // words of B per CTA in the group solve (a near-full-rank matrix has one)
 constexpr int TWG = 1;   // words of B per CTA in the bulk update
 static_assert(TWG == 1, "the bulk update's lookups assume one word per tile");
 
