@@ -71,6 +71,8 @@ extern "C" {
 #define GF2_PRODUCT_AUTO 0
 #define GF2_PRODUCT_XOR 1    /* Gray-code XOR tables (Method of the Four Russians) */
 #define GF2_PRODUCT_TENSOR 2 /* 0/1 operands on the tensor cores, exact, low bit kept */
+#define GF2_PRODUCT_STRASSEN 3        /* Strassen-Winograd recursion, XOR-table leaves (gf2_mul only) */
+#define GF2_PRODUCT_STRASSEN_TENSOR 4 /* Strassen-Winograd recursion, tensor-core leaves (gf2_mul only) */
 
 /*
  * Tuning knobs. None of them changes any result (rank, P, Q, L, S and RREF
@@ -82,7 +84,8 @@ typedef struct gf2_opts {
     int tile_words;     /* column tile of a table sweep, in words: 0 (default), 4, 8 or 16 */
     int grid_ctas;      /* CTAs of a table sweep; 0 = one per SM but one (left to the overlapping pivot search) */
     int product;        /* GF2_PRODUCT_*; used by gf2_mul */
-    int64_t cutoff_cols;/* recursive PLS: MMPF base case at or below this many columns (Sec. 6); 0 = MMPF only */
+    int64_t cutoff_cols;/* recursive PLS: MMPF base case at or below this many columns (Sec. 6); 0 = MMPF only.
+                           Strassen products: the smallest dimension recursed on (0 = 8192) */
     int reserved[8];    /* must be zero */
 } gf2_opts;
 
@@ -90,10 +93,20 @@ typedef struct gf2_opts {
  * Bytes of workspace an operation needs for an m x n matrix. For GF2_OP_MUL
  * pass the inner dimension k as m and the column count n as n: the tensor-core
  * product keeps B transposed there (n x ceil(k/64) words, rounded to whole
- * 128-bit chunks); the XOR-table product needs none. Returns 0 for invalid
- * sizes.
+ * 128-bit chunks); the XOR-table product needs none; the Strassen forms are
+ * sized for a k x k A (use gf2_mul_workspace_bytes for any shape). Returns 0
+ * for invalid sizes.
  */
 size_t gf2_workspace_bytes(int op, int64_t m, int64_t n, const gf2_opts *opts);
+
+/*
+ * Workspace bytes of gf2_mul for A m x k, B k x n under opts->product: 0 for the
+ * XOR-table form; B^T for the tensor-core form; for the Strassen forms, the
+ * product A.B when accumulating, each level's three block temporaries
+ * (m/2 x k/2, k/2 x n/2, m/2 x n/2 at the top, a quarter of that per level
+ * down) and the leaf's own. Returns 0 for invalid arguments.
+ */
+size_t gf2_mul_workspace_bytes(int64_t m, int64_t k, int64_t n, const gf2_opts *opts);
 
 /*
  * PLS decomposition with rank, in place (Proposition "PLS decomposition";
@@ -137,8 +150,13 @@ int gf2_rank(const uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *r
  * Product over GF(2): C = A.B (accumulate == 0) or C = C + A.B (accumulate
  * != 0), the trailing update A_SE <- A_SE + A_SW.A_NE of Algorithm PLS
  * (Sec. 5). A is m x k, B is k x n, C is m x n, each with its own stride.
- * C must not overlap A or B. opts->product picks the XOR-table form or the
- * tensor-core form (bit-exact in both).
+ * C must not overlap A or B. opts->product picks the XOR-table form, the
+ * tensor-core form, or Strassen-Winograd recursion over either (7 half-size
+ * products and 15 block XORs per level, taken while m, k, n >= 2 x leaf size
+ * and k, n are multiples of 2048; the leaf size is opts->cutoff_cols, default
+ * 8192). All forms are bit-exact. work may be NULL (an internal workspace is
+ * used), else it holds at least gf2_mul_workspace_bytes(m, k, n, opts) bytes
+ * (GF2_ENOSPACE otherwise).
  */
 int gf2_mul(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64_t *B, int64_t sb,
             int64_t m, int64_t k, int64_t n, int accumulate, void *work, size_t work_bytes,

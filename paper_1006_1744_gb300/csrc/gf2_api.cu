@@ -147,7 +147,7 @@ int check_opts(const gf2_opts *o)
         return GF2_EINVAL;
     if (o->tile_words != 0 && o->tile_words != 4 && o->tile_words != 8 && o->tile_words != 16)
         return GF2_EINVAL;
-    if (o->grid_ctas < 0 || o->product < 0 || o->product > 2 || o->cutoff_cols < 0)
+    if (o->grid_ctas < 0 || o->product < 0 || o->product > GF2_PRODUCT_STRASSEN_TENSOR || o->cutoff_cols < 0)
         return GF2_EINVAL;
     if (o->cutoff_cols != 0 && o->cutoff_cols < 128)
         return GF2_EINVAL;
@@ -239,7 +239,9 @@ size_t gf2_workspace_bytes(int op, int64_t m, int64_t n, const gf2_opts *opts)
     case GF2_OP_RREF:
     case GF2_OP_RANK:
         return elim_layout(op, m, n).total;
-    case GF2_OP_MUL:  // (m, n) = (inner dimension k, columns n)
+    case GF2_OP_MUL:  // (m, n) = (inner dimension k, columns n); Strassen forms: a k x k A assumed
+        if (opts && (opts->product == GF2_PRODUCT_STRASSEN || opts->product == GF2_PRODUCT_STRASSEN_TENSOR))
+            return gf2_mul_workspace_bytes(m, m, n, opts);
         return align_up(mul_tensor_workspace(0, m, n), 256);
     default:
         return 0;
@@ -356,6 +358,18 @@ int gf2_mul(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64
     if (!C)
         return GF2_EINVAL;
     const int product = opts ? opts->product : GF2_PRODUCT_AUTO;
+    if (product == GF2_PRODUCT_STRASSEN || product == GF2_PRODUCT_STRASSEN_TENSOR) {
+        const int kind = product == GF2_PRODUCT_STRASSEN ? GF2_PRODUCT_XOR : GF2_PRODUCT_TENSOR;
+        const int64_t leaf = (opts && opts->cutoff_cols) ? opts->cutoff_cols : STRASSEN_LEAF_DEFAULT;
+        const size_t need = mul_strassen_workspace(m, k, n, leaf, kind);
+        if (need && (rc = get_work(work, work_bytes, need)))
+            return rc;
+        if (kind == GF2_PRODUCT_XOR && k == 0 && !accumulate)
+            return note_cuda(cudaMemset2DAsync(C, (size_t)sc * 8, 0, (size_t)((n + 63) / 64) * 8, (size_t)m, s));
+        if (kind == GF2_PRODUCT_XOR && k == 0)
+            return GF2_OK;
+        return mul_strassen(C, sc, A, sa, B, sb, m, k, n, accumulate, work, work_bytes, leaf, kind, s);
+    }
     if (product == GF2_PRODUCT_TENSOR) {
         const size_t need = mul_tensor_workspace(m, k, n);
         if ((rc = get_work(work, work_bytes, need)))
@@ -371,6 +385,22 @@ int gf2_mul(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64
     }
     return mul_xor(C, sc, A, sa, B, sb, m, k, n, accumulate, opts ? opts->tile_words : 0,
                    opts ? opts->grid_ctas : 0, s);
+}
+
+size_t gf2_mul_workspace_bytes(int64_t m, int64_t k, int64_t n, const gf2_opts *opts)
+{
+    if (check_opts(opts) || m < 0 || k < 0 || n < 0 || m > INT32_MAX - 64 || k > INT32_MAX - 64 ||
+        n > INT32_MAX - 64)
+        return 0;
+    const int product = opts ? opts->product : GF2_PRODUCT_AUTO;
+    if (product == GF2_PRODUCT_STRASSEN || product == GF2_PRODUCT_STRASSEN_TENSOR) {
+        const int kind = product == GF2_PRODUCT_STRASSEN ? GF2_PRODUCT_XOR : GF2_PRODUCT_TENSOR;
+        const int64_t leaf = (opts && opts->cutoff_cols) ? opts->cutoff_cols : STRASSEN_LEAF_DEFAULT;
+        return align_up(mul_strassen_workspace(m, k, n, leaf, kind), 256);
+    }
+    if (product == GF2_PRODUCT_TENSOR)
+        return align_up(mul_tensor_workspace(m, k, n), 256);
+    return 0;
 }
 
 const char *gf2_strerror(int code)

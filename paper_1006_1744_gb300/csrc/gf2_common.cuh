@@ -285,6 +285,13 @@ int mul_xor(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64
 int mul_tensor(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64_t *B, int64_t sb,
                int64_t m, int64_t k, int64_t n, int acc, void *work, size_t work_bytes, cudaStream_t s);
 size_t mul_tensor_workspace(int64_t m, int64_t k, int64_t n);
+// Strassen-Winograd product (gf2_strassen.cu): leaf = smallest dimension recursed on,
+// leaf_kind = GF2_PRODUCT_XOR or GF2_PRODUCT_TENSOR
+constexpr int64_t STRASSEN_LEAF_DEFAULT = 8192;
+size_t mul_strassen_workspace(int64_t m, int64_t k, int64_t n, int64_t leaf, int leaf_kind);
+int mul_strassen(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64_t *B, int64_t sb, int64_t m,
+                 int64_t k, int64_t n, int accumulate, void *work, size_t work_bytes, int64_t leaf, int leaf_kind,
+                 cudaStream_t s);
 // recursive PLS (gf2_rec.cu)
 size_t rec_workspace_bytes(int64_t m, int64_t n, int64_t cutoff);
 int pls_recursive(uint64_t *A, int64_t stride, int64_t m, int64_t n, int64_t *P, int64_t *Q, int64_t *rank,

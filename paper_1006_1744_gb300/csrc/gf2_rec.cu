@@ -382,7 +382,9 @@ static int pls_rec(uint64_t *A, int64_t stride, int64_t m, int64_t n, int64_t *P
             return rc;
         // A_SE <- A_SE + A_SW . A_NE
         if (m > r0) {
-            const int product = opts->product == GF2_PRODUCT_TENSOR ? GF2_PRODUCT_TENSOR : GF2_PRODUCT_XOR;
+            const int product = (opts->product == GF2_PRODUCT_TENSOR || opts->product == GF2_PRODUCT_STRASSEN_TENSOR)
+                                    ? GF2_PRODUCT_TENSOR
+                                    : GF2_PRODUCT_XOR;
             if (product == GF2_PRODUCT_TENSOR)
                 rc = mul_tensor(A1 + r0 * stride, stride, A + r0 * stride, stride, A1, stride, m - r0, r0, n - n0, 1,
                                 w.bt, w.bt_bytes, s);

@@ -21,7 +21,7 @@ _lock = threading.Lock()
 _lib = None
 
 OP_PLS, OP_RREF, OP_RANK, OP_MUL = 1, 2, 3, 4
-PRODUCT_AUTO, PRODUCT_XOR, PRODUCT_TENSOR = 0, 1, 2
+PRODUCT_AUTO, PRODUCT_XOR, PRODUCT_TENSOR, PRODUCT_STRASSEN, PRODUCT_STRASSEN_TENSOR = 0, 1, 2, 3, 4
 
 _i64 = ctypes.c_int64
 _vp = ctypes.c_void_p
@@ -49,6 +49,7 @@ class BatchItem(ctypes.Structure):
 
 SYMBOLS = {
     "gf2_workspace_bytes": (_sz, [_int, _i64, _i64, _vp]),
+    "gf2_mul_workspace_bytes": (_sz, [_i64, _i64, _i64, _vp]),
     "gf2_pls": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp, _sz, _vp, _vp]),
     "gf2_rref": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _vp, _sz, _vp, _vp]),
     "gf2_rank": (_int, [_vp, _i64, _i64, _i64, _vp, _vp, _sz, _vp, _vp]),
@@ -227,6 +228,11 @@ def rank_noalloc(A: torch.Tensor, n: int, rank=None, stream=None):
     rank = torch.empty(1, dtype=torch.int64, device=A.device) if rank is None else rank
     _check(lib().gf2_rank_noalloc(_ptr(A), m, n, stride, _ptr(rank), _stream(stream)), "gf2_rank_noalloc")
     return rank
+
+
+def mul_workspace_bytes(m: int, k: int, n: int, opts=None) -> int:
+    """Workspace bytes of mul() for A m x k and B k x n under opts (0 = none needed)."""
+    return int(lib().gf2_mul_workspace_bytes(m, k, n, _opts(opts)))
 
 
 def mul(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, m: int, k: int, n: int, accumulate=False,

@@ -138,3 +138,22 @@ def test_autotune_argument_checks_host_only(built):
     assert L.gf2_autotune(gf2.OP_PLS, 64, 64, 0.0, byref(o), byref(ms), None) == 1
     assert L.gf2_autotune(gf2.OP_PLS, 64, 64, 1.5, byref(o), byref(ms), None) == 1
     assert L.gf2_autotune(gf2.OP_PLS, 64, 64, 0.5, None, byref(ms), None) == 1
+
+
+def test_mul_workspace_bytes_by_product_form():
+    """The product's workspace query: none for the XOR-table form, B^T for the
+    tensor-core form, and for the Strassen forms a size that grows with the
+    recursion and is zero-cost only when no level is taken."""
+    from paper_1006_1744_gb300 import gf2
+    assert gf2.mul_workspace_bytes(4096, 4096, 4096, {"product": 1}) == 0
+    tc = gf2.mul_workspace_bytes(4096, 4096, 4096, {"product": 2})
+    assert tc >= 4096 * 4096 // 8
+    one = gf2.mul_workspace_bytes(4096, 4096, 4096, {"product": 3, "cutoff_cols": 2048})   # one level
+    two = gf2.mul_workspace_bytes(4096, 4096, 4096, {"product": 3, "cutoff_cols": 1024})   # two levels
+    assert 0 < one < two
+    # the accumulation product (m x n) plus at least the top level's three blocks
+    assert one >= 4096 * 4096 // 8 + 3 * (2048 * 2048 // 8)
+    assert gf2.mul_workspace_bytes(4096, 3000, 4096, {"product": 3, "cutoff_cols": 1024}) == 0  # no split
+    assert gf2.mul_workspace_bytes(4096, 4096, 4096, {"product": 4, "cutoff_cols": 1024}) > two
+    assert gf2.mul_workspace_bytes(-1, 4, 4, None) == 0
+    assert gf2.mul_workspace_bytes(64, 64, 64, {"product": 5}) == 0

@@ -257,6 +257,44 @@ def test_mul_parity(g, acc):
         assert (host(Cd)[:, :W] == want[:, :W]).all()
 
 
+@pytest.mark.parametrize("product", [3, 4])
+@pytest.mark.parametrize("acc", [False, True])
+def test_mul_strassen_parity(g, product, acc):
+    """Strassen-Winograd products (XOR-table and tensor-core leaves) equal the
+    plain product bit for bit: leaf size 512 gives up to three levels here, and
+    shapes that do not split fall back to the leaf form."""
+    rng = np.random.default_rng(11 + product + 2 * acc)
+    opts = {"product": product, "cutoff_cols": 512}
+    for (m, k, n) in [(2048, 2048, 2048), (4096, 2048, 4096), (2048, 4096, 2048), (4096, 4096, 4096),
+                      (1000, 2048, 2048), (2048, 3000, 2048), (1024, 1024, 1024)]:
+        A = S.dense(m, k, int(rng.integers(1 << 30)))
+        B = S.dense(k, n, int(rng.integers(1 << 30)))
+        C0 = S.dense(m, n, int(rng.integers(1 << 30)))
+        want = oracle.mul(A, B, m, k, n, C=C0 if acc else None, stride=C0.shape[1])
+        Cd = dev(C0)
+        nb = g.mul_workspace_bytes(m, k, n, opts)
+        work = torch.empty(max(nb // 8, 1) + 32, dtype=torch.int64, device="cuda")
+        g.mul(Cd, dev(A), dev(B), m, k, n, accumulate=acc, work=work, opts=opts)
+        torch.cuda.synchronize()
+        W = S.words_per_row(n)
+        assert (host(Cd)[:, :W] == want[:, :W]).all(), (m, k, n)
+
+
+def test_mul_strassen_internal_workspace_and_too_small(g):
+    m = k = n = 4096
+    opts = {"product": 3, "cutoff_cols": 1024}
+    A = S.dense(m, k, 5)
+    B = S.dense(k, n, 6)
+    want = oracle.mul(A, B, m, k, n)
+    Cd = torch.zeros((m, S.default_stride(n)), dtype=torch.int64, device="cuda")
+    g.mul(Cd, dev(A), dev(B), m, k, n, opts=opts)  # internal workspace
+    torch.cuda.synchronize()
+    assert (host(Cd) == want).all()
+    small = torch.empty(64, dtype=torch.int64, device="cuda")
+    with pytest.raises(g.Gf2Error):
+        g.mul(Cd, dev(A), dev(B), m, k, n, work=small, opts=opts)
+
+
 def test_device_generator_matches_host(g):
     from paper_1006_1744_gb300 import synth_gpu
     for (m, n) in [(1, 1), (70, 130), (300, 64), (257, 1000)]:
