@@ -244,7 +244,8 @@ int gf2_diag_wait_timeout(uint64_t limit_ns, void *stream);
  *     the recursive split at 4096 columns with the XOR-table and the
  *     tensor-core product;
  *   GF2_OP_MUL (C = A.B with A m x n, B n x n): the XOR-table and the
- *     tensor-core product.
+ *     tensor-core product, and where a level applies (m, n >= 16384, n a
+ *     multiple of 2048) Strassen-Winograd over either.
  * The answer is cached per (device, op, ceil(log2 m), ceil(log2 n), density
  * bucket {>= 0.3, >= 0.03, less}); a repeated call returns it without timing.
  * GF2_EINVAL for bad arguments, GF2_ENOMEM if no candidate fits in memory.

@@ -93,6 +93,12 @@ extern "C" int gf2_autotune(int op, int64_t m, int64_t n, double density, gf2_op
     if (op == GF2_OP_MUL) {
         cands.push_back(opt(0, 0, GF2_PRODUCT_XOR));
         cands.push_back(opt(0, 0, GF2_PRODUCT_TENSOR));
+        // Strassen-Winograd over either leaf, where at least one level applies
+        const int64_t leaf = gf2::STRASSEN_LEAF_DEFAULT;
+        if (m % 2 == 0 && n % 2048 == 0 && m >= 2 * leaf && n >= 2 * leaf) {
+            cands.push_back(opt(0, 0, GF2_PRODUCT_STRASSEN));
+            cands.push_back(opt(0, 0, GF2_PRODUCT_STRASSEN_TENSOR));
+        }
     } else {
         for (int tw : {4, 8, 16})
             cands.push_back(opt(tw, 0, 0));
@@ -128,9 +134,9 @@ extern "C" int gf2_autotune(int op, int64_t m, int64_t n, double density, gf2_op
     gf2_opts best_opts{};
     int rc = GF2_OK;
     for (const gf2_opts &o : cands) {
-        // the product's workspace is sized by its inner dimension (n here) and columns
-        const size_t need = op == GF2_OP_MUL ? gf2_workspace_bytes(op, n, n, &o) : gf2_workspace_bytes(op, m, n, &o);
-        if (!need) {
+        // a product's workspace depends on its form (none for the XOR-table form)
+        const size_t need = op == GF2_OP_MUL ? gf2_mul_workspace_bytes(m, n, n, &o) : gf2_workspace_bytes(op, m, n, &o);
+        if (!need && op != GF2_OP_MUL) {
             rc = GF2_EINVAL;
             break;
         }

@@ -295,6 +295,23 @@ def test_mul_strassen_internal_workspace_and_too_small(g):
         g.mul(Cd, dev(A), dev(B), m, k, n, work=small, opts=opts)
 
 
+def test_autotune_product_with_strassen_candidates(g):
+    """At 16384^2 the product's candidates include both Strassen forms; whatever
+    is chosen gives the same product as the XOR-table form."""
+    from paper_1006_1744_gb300 import synth_gpu
+    n = 16384
+    om, ms = g.autotune(g.OP_MUL, n, n, 0.5)
+    assert om["product"] in (1, 2, 3, 4) and ms > 0
+    A = synth_gpu.dense(n, n, 21)
+    B = synth_gpu.dense(n, n, 22)
+    ref = torch.zeros_like(A)
+    g.mul(ref, A, B, n, n, n, opts={"product": 1})
+    C = torch.zeros_like(A)
+    g.mul(C, A, B, n, n, n, opts=om)
+    torch.cuda.synchronize()
+    assert torch.equal(C, ref)
+
+
 def test_device_generator_matches_host(g):
     from paper_1006_1744_gb300 import synth_gpu
     for (m, n) in [(1, 1), (70, 130), (300, 64), (257, 1000)]:
