@@ -193,25 +193,32 @@ int gf2_pls_batched(const gf2_batch_item *items, int64_t count, int64_t *ranks, 
                     const gf2_opts *opts, void *stream);
 
 /*
- * Rank without allocating device memory. The paper has no counterpart: this
- * entry point exists for callers that may not call cudaMalloc -- code that runs
- * while a CUDA graph is being captured, loops that cannot afford the device
- * stall an allocation brings, and plug-ins whose host application owns all
- * device memory. It computes exactly what gf2_rank computes (same arguments,
- * A unchanged), but its workspace is one fixed array of
+ * Rank without allocating device memory. The paper has no counterpart. Some
+ * callers cannot call cudaMalloc: a plug-in inside a host application that
+ * owns the whole device-memory budget is not allowed to; a latency-bound loop
+ * cannot take the device-wide synchronisation and the milliseconds cudaMalloc
+ * and cudaFree may cost; a process whose device memory is already reserved by
+ * another framework's caching allocator may see the allocation fail. This
+ * entry point computes exactly what gf2_rank computes (same arguments, A
+ * unchanged), but its workspace is one fixed array of
  * GF2_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU that
- * loads the library holds until the process exits. Nothing is allocated or
- * freed by any call.
+ * loads the library holds until the process exits. No call allocates or frees
+ * device memory, and none is recorded into or replayed from a library-owned
+ * CUDA graph: each call enqueues the elimination directly on `stream` (and on
+ * a side stream of the library, ordered by events).
  *   Limit: matrices whose rank workspace, gf2_workspace_bytes(GF2_OP_RANK, m,
- *   n, NULL), exceeds GF2_NOALLOC_SCRATCH_BYTES (4 MiB; e.g. 4096 x 4096 fits)
- *   are refused with GF2_ETOOBIG before anything is enqueued.
- *   First call per device: looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.
- *   Sharing: every call on a device uses that device's one array, which
- *   keeps the last call's contents (each call re-initialises everything it
- *   reads). Calls whose work can overlap on the GPU, e.g. on two streams of
- *   the same device, race on the array; order them on one stream.
+ *   n, NULL), exceeds GF2_NOALLOC_SCRATCH_BYTES (4 MiB; e.g. 4096 x 4096 fits,
+ *   8192 x 8192 does not) are refused with GF2_ETOOBIG before anything is
+ *   enqueued. Other argument errors are those of gf2_rank.
+ *   First call per device: with that device current, it looks up the array's
+ *   device address (cudaGetSymbolAddress) and creates the side stream and
+ *   three events it reuses from then on; make that first call before any
+ *   stream capture.
+ *   Sharing: every call on a device uses that device's one array, which keeps
+ *   the last call's contents (each call re-initialises everything it reads).
+ *   Calls whose work can overlap on the GPU, e.g. on two streams of the same
+ *   device, race on the array; order them on one stream. Concurrent host
+ *   threads are serialised while they enqueue.
  */
 #define GF2_NOALLOC_SCRATCH_BYTES (4u << 20)
 int gf2_rank_noalloc(const uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *rank, void *stream);

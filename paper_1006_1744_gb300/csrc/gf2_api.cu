@@ -199,6 +199,25 @@ int pls_base(uint64_t *A, int64_t stride, int64_t m, int64_t n, int64_t *P, int6
     return note_cuda(cudaMemcpyAsync(perm_out, e.perm, (size_t)m * sizeof(int), cudaMemcpyDeviceToDevice, s));
 }
 
+// Rank of A (left unchanged) by one direct elimination of a copy held in `work`: no graph
+// replay and no allocation; the side stream and events come from the caller.
+int rank_direct(const uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *rank, char *work,
+                const ElimAux &aux, cudaStream_t s)
+{
+    if (m == 0 || n == 0)
+        return identity_fill(nullptr, 0, nullptr, 0, rank, s);
+    const ElimLayout L = elim_layout(GF2_OP_RANK, m, n);
+    uint64_t *copy = reinterpret_cast<uint64_t *>(work + L.out);
+    const int64_t cs = min_stride(n);
+    const Elim e = make_elim(copy, m, n, cs, work, L, nullptr, nullptr, false, nullptr, s);
+    const cudaError_t err = cudaMemcpy2DAsync(copy, (size_t)cs * 8, A, (size_t)stride * 8,
+                                              (size_t)((n + 63) / 64) * 8, (size_t)m, cudaMemcpyDeviceToDevice, s);
+    if (err != cudaSuccess)
+        return note_cuda(err);
+    const int rc = elim_run(e, aux);
+    return rc ? rc : elim_gather(e, rank);
+}
+
 static CallKey call_key(int op, const void *A, int64_t m, int64_t n, int64_t stride, const void *P, const void *Q,
                         const void *rank, const void *pivots, const void *work, size_t work_bytes, const Elim &e)
 {

@@ -273,6 +273,17 @@ int sweep_ctas_per_sm(int tile_words);
 
 // panel elimination: runs every panel; afterwards st->r_next is the rank.
 int elim_run(const Elim &e);
+// The same, with the side stream and the three ordering events supplied by the caller
+// (elim_run(e) takes a side stream of the device and creates and releases its own events).
+struct ElimAux {
+    cudaStream_t side;
+    cudaEvent_t ev[3];
+};
+int elim_run(const Elim &e, const ElimAux &aux);
+// rank of A (unchanged) by a direct elimination of a copy in work (gf2_api.cu): never replayed
+// from a graph, allocates nothing
+int rank_direct(const uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *rank, char *work,
+                const ElimAux &aux, cudaStream_t s);
 // writes P/Q identity fill, rank, gathers rows into e.out in final order
 int elim_gather(const Elim &e, int64_t *rank);
 // compress L in e.out and copy e.out back into e.A

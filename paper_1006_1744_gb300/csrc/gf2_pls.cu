@@ -1543,17 +1543,26 @@ int capture_streams(cudaStream_t *origin, cudaStream_t *side)
 // states and side buffers alternate with the parity of b.
 int elim_run(const Elim &e)
 {
+    ElimAux aux{};
+    EventSet E;
+    int rc;
+    if ((rc = side_stream(&aux.side)) || (rc = E.create()))
+        return rc;
+    for (int i = 0; i < 3; ++i)
+        aux.ev[i] = E.ev[i];
+    return elim_run(e, aux);
+}
+
+int elim_run(const Elim &e, const ElimAux &aux)
+{
     const int m = (int)e.m;
     k_init<<<(m + 255) / 256, 256, 0, e.s>>>(e.A, e.stride, e.perm, e.side, e.st, m);
     prof_launched(1);
     int rc = note_cuda(cudaGetLastError());
     if (rc || e.W == 0)
         return rc;
-    cudaStream_t t = nullptr;
-    EventSet E;
-    if ((rc = side_stream(&t)) || (rc = E.create()))
-        return rc;
-    cudaEvent_t ev_piv = E.ev[0], ev_rest[2] = {E.ev[1], E.ev[2]};
+    cudaStream_t t = aux.side;
+    cudaEvent_t ev_piv = aux.ev[0], ev_rest[2] = {aux.ev[1], aux.ev[2]};
     for (int b = 0; b < (int)e.W; ++b) {
         const int nbits = (int)((e.n - 64ll * b) < 64 ? (e.n - 64ll * b) : 64);
         const u64 *prev = e.side + (size_t)((b + 1) & 1) * e.m;  // panel word b - 1 of every row
