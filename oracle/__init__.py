@@ -39,6 +39,36 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_LIB_OMP = os.path.join(_HERE, "liboracle_gf2_omp.so")
+_lib_omp = None
+
+
+def build_omp(force: bool = False) -> str:
+    """The same source compiled with OpenMP (only gf2o_pls_omp differs): the all-cores timing variant."""
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC):
+        tmp = _LIB_OMP + ".tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
+def pls_omp(A: np.ndarray, m: int, n: int):
+    """Gaussian PLS with OpenMP threads over the rows of each step (timing variant; same result)."""
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            build_omp()
+            lib = ctypes.CDLL(_LIB_OMP)
+            lib.gf2o_pls_omp.restype = _i64
+            lib.gf2o_pls_omp.argtypes = [_p, _i64, _i64, _i64, _p, _p]
+            _lib_omp = lib
+    A = _mat(A).copy()
+    P = np.zeros(max(m, 1), dtype=np.int64)
+    Q = np.zeros(max(n, 1), dtype=np.int64)
+    r = _lib_omp.gf2o_pls_omp(_ptr(A), m, n, A.shape[1], _ptr(P), _ptr(Q))
+    return A, P[:m], Q[:n], int(r)
+
+
 def _load():
     global _lib
     with _lock:
@@ -55,6 +85,8 @@ def _load():
             lib.gf2o_pls_mmpf.argtypes = [_p, _i64, _i64, _i64, _p, _p, ctypes.c_int]
             lib.gf2o_pls_rec.restype = _i64
             lib.gf2o_pls_rec.argtypes = [_p, _i64, _i64, _i64, _p, _p, _i64, ctypes.c_int, ctypes.c_int]
+            lib.gf2o_m4ri.restype = _i64
+            lib.gf2o_m4ri.argtypes = [_p, _i64, _i64, _i64, ctypes.c_int, _p]
             lib.gf2o_make_table.restype = None
             lib.gf2o_make_table.argtypes = [_p, _i64, _i64, _i64, ctypes.c_int, _i64, ctypes.c_int, _p, _i64, _p]
             lib.gf2o_add_rows_from_table.restype = None
@@ -129,6 +161,16 @@ def pls_rec(A: np.ndarray, m: int, n: int, cutoff: int, k: int, split_words: boo
     r = _load().gf2o_pls_rec(_ptr(A), m, n, A.shape[1], _ptr(P), _ptr(Q), cutoff, k, int(split_words))
     assert r >= 0
     return A, P[:m], Q[:n], int(r)
+
+
+def m4ri(A: np.ndarray, m: int, n: int, k: int):
+    """Literal Algorithm M4RI (GaussSubmatrix, MakeTable, AddRowsFromTable above and below).
+    Returns (R, pivots (len r), r) like rref()."""
+    A = _mat(A).copy()
+    piv = np.zeros(max(min(m, n), 1), dtype=np.int64)
+    r = _load().gf2o_m4ri(_ptr(A), m, n, A.shape[1], k, _ptr(piv))
+    assert r >= 0
+    return A, piv[:r], int(r)
 
 
 def make_table(A: np.ndarray, n: int, r: int, k: int, c: int, fix: bool):

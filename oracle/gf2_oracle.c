@@ -22,6 +22,8 @@
  *   gf2o_pls_mmpf -- Algorithm MMPF with PlsSubmatrix (Sec. 4.1, appendix).
  *   gf2o_pls_rec  -- Algorithm "PLS Decomposition" (Sec. 5), recursive, with
  *                    MMPF as the base case below a column cutoff (Sec. 6).
+ *   gf2o_m4ri     -- Algorithm M4RI with GaussSubmatrix (Sec. 3.1, appendix):
+ *                    the reduced row echelon form without PLS.
  *
  * Readings of the paper where it is garbled or silent (each listed in the
  * design notes): swap vectors P, Q (transpositions i <-> P[i] applied in
@@ -130,6 +132,56 @@ int64_t gf2o_pls(uint64_t *A, int64_t m, int64_t n, int64_t s, int64_t *P, int64
         Q[i] = i;
     for (int64_t j = 0; j < r; ++j)
         swap_cols_from(A, s, m, j, Q[j], j);
+    return r;
+}
+
+/*
+ * The same Gaussian PLS, timed as the all-cores CPU baseline: within each
+ * pivot step the rows below the pivot are independent, and so are the rows
+ * during the final column swaps, so those two loops are spread over threads
+ * when the file is compiled with OpenMP (liboracle_gf2_omp.so). The result is
+ * gf2o_pls's, bit for bit; compiled without OpenMP it is gf2o_pls.
+ */
+int64_t gf2o_pls_omp(uint64_t *A, int64_t m, int64_t n, int64_t s, int64_t *P, int64_t *Q)
+{
+    int64_t r = 0, c = 0;
+    while (r < m && c < n) {
+        int64_t pi = -1, pj = -1;
+        for (int64_t j = c; j < n && pi < 0; ++j) {
+            for (int64_t i = r; i < m; ++i) {
+                if (getb(A, s, i, j)) {
+                    pi = i;
+                    pj = j;
+                    break;
+                }
+            }
+        }
+        if (pi < 0)
+            break;
+        P[r] = pi;
+        Q[r] = pj;
+        swap_rows(A, s, n, r, pi);
+        if (pj + 1 < n) {
+#pragma omp parallel for schedule(static)
+            for (int64_t l = r + 1; l < m; ++l)
+                if (getb(A, s, l, pj))
+                    add_row_from(A, s, n, l, r, pj + 1);
+        }
+        r += 1;
+        c = pj + 1;
+    }
+    for (int64_t i = r; i < m; ++i)
+        P[i] = i;
+    for (int64_t i = r; i < n; ++i)
+        Q[i] = i;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < r && j <= i; ++j)
+            if (Q[j] != j) {
+                int va = getb(A, s, i, j), vb = getb(A, s, i, Q[j]);
+                setb(A, s, i, j, vb);
+                setb(A, s, i, Q[j], va);
+            }
     return r;
 }
 
@@ -426,6 +478,84 @@ int64_t gf2o_pls_mmpf(uint64_t *A, int64_t m, int64_t n, int64_t s, int64_t *P, 
     if (k < 1 || k > 16)
         return -1;
     return mmpf_view(whole(A, m, n, s), P, Q, k);
+}
+
+/*
+ * GaussSubmatrix (appendix; used by Algorithm M4RI, Sec. 3.1): Gauss-Jordan
+ * elimination of the k columns c .. c+k-1 over the rows r .. r_end-1. For
+ * column j, each candidate row i (from the next free row r_s on) first has
+ * its bits at the block's earlier columns cleared by the block's pivot rows
+ * (pivot row r+l clears column c+l, added from that column on); the first
+ * candidate left with a 1 at column j is swapped to row r_s and added (from
+ * column j on) to the block's earlier pivot rows that have a 1 at column j.
+ * Returns the number of consecutive columns from c that got a pivot (it stops
+ * at the first column without one).
+ */
+static int gauss_submatrix(view_t A, int64_t r, int64_t c, int k, int64_t r_end)
+{
+    int64_t rs = r;
+    for (int64_t j = c; j < c + k; ++j) {
+        int found = 0;
+        for (int64_t i = rs; i < r_end; ++i) {
+            for (int64_t l = 0; l < j - c; ++l)
+                if (vget(A, i, c + l))
+                    vadd_row(A, i, r + l, c + l);
+            if (vget(A, i, j)) {
+                vswap_rows(A, i, rs);
+                for (int64_t l = r; l < rs; ++l)
+                    if (vget(A, l, j))
+                        vadd_row(A, l, rs, j);
+                rs += 1;
+                found = 1;
+                break;
+            }
+        }
+        if (!found)
+            return (int)(j - c);
+    }
+    return k;
+}
+
+/*
+ * Algorithm M4RI (Sec. 3.1): reduced row echelon form, in place. Per step,
+ * GaussSubmatrix finds kbar <= k pivots in consecutive columns from c (the
+ * block becomes the identity there), MakeTable enumerates the 2^kbar sums of
+ * those rows from column c on, and AddRowsFromTable clears the kbar columns
+ * in every other row, above (rows 0 .. r-1) and below (rows r+kbar .. m-1).
+ * A column without a pivot is skipped. k shrinks to n - c near the right end.
+ * pivots (nullable, length >= rank) receives the pivot columns. Returns the
+ * rank, or -1 for k outside 1 .. 16.
+ */
+int64_t gf2o_m4ri(uint64_t *A, int64_t m, int64_t n, int64_t s, int k, int64_t *pivots)
+{
+    if (k < 1 || k > 16)
+        return -1;
+    view_t V = whole(A, m, n, s);
+    int64_t ts = (n + 63) / 64 + 1;
+    uint64_t *Tbuf = (uint64_t *)calloc((size_t)(((int64_t)1 << k) * ts), sizeof(uint64_t));
+    int64_t *L = (int64_t *)calloc((size_t)1 << k, sizeof(int64_t));
+    int64_t r = 0, c = 0;
+    while (c < n) {
+        if (c + k > n)
+            k = (int)(n - c);
+        int kbar = gauss_submatrix(V, r, c, k, m);
+        if (kbar > 0) {
+            view_t T = whole(Tbuf, (int64_t)1 << kbar, n, ts);
+            vmake_table(sub(V, r, 0, kbar, n), kbar, c, 0, T, L);
+            vadd_rows_from_table(V, 0, r, c, kbar, T, L);
+            vadd_rows_from_table(V, r + kbar, m, c, kbar, T, L);
+            if (pivots)
+                for (int t = 0; t < kbar; ++t)
+                    pivots[r + t] = c + t;
+        }
+        r += kbar;
+        c += kbar;
+        if (k != kbar)
+            c += 1;
+    }
+    free(Tbuf);
+    free(L);
+    return r;
 }
 
 /*

@@ -337,6 +337,42 @@ def test_rref_unique_idempotent_structured(kind):
         assert oracle.rank(S.pack(stack), stack.shape[0], n) == r
 
 
+@pytest.mark.parametrize("kind", KINDS)
+def test_m4ri_reaches_the_unique_rref(kind):
+    """Algorithm M4RI (Sec. 3.1) gives the reduced row echelon form, which is
+    unique (Sec. 2): its result, rank and pivots equal Gauss-Jordan's for every
+    table width k, and the structural checks of a reduced echelon form hold."""
+    rng = np.random.default_rng(41 + len(kind))
+    for trial in range(12):
+        m = int(rng.integers(1, 70))
+        n = int(rng.integers(1, 140))
+        A = _inputs(rng, m, n, kind, 6000 + trial)
+        R, piv, r = oracle.rref(A, m, n)
+        for k in (1, 2, 3, 5, 8):
+            R4, piv4, r4 = oracle.m4ri(A, m, n, k)
+            assert r4 == r and (piv4 == piv).all(), (kind, m, n, k)
+            W = S.words_per_row(n)
+            assert (R4[:, :W] == R[:, :W]).all(), (kind, m, n, k)
+            assert is_rref(S.unpack(R4, m, n), r4)
+
+
+def test_m4ri_worked_example_golden():
+    """The M4RI idea of Sec. 3.1 on its printed example (Figure 1): the three
+    rows A0..A2 are the identity on the first k = 3 columns, and the row with
+    index bits 110 becomes ROW_AFTER once T[110] is added. M4RI with k = 3 on
+    [A0; A1; A2; ROW_BEFORE] does exactly that first step; ROW_AFTER is then a
+    single 1, so it is the last row of the reduced form, which equals
+    Gauss-Jordan's."""
+    g = _golden("fig1_maketable.txt")
+    M = np.stack([g["A0"], g["A1"], g["A2"], g["ROW_BEFORE"]])
+    m, n = M.shape
+    assert int(g["ROW_AFTER"].sum()) == 1
+    R4, piv4, r4 = oracle.m4ri(S.pack(M), m, n, 3)
+    R, piv, r = oracle.rref(S.pack(M), m, n)
+    assert r4 == r == 4 and (piv4 == piv).all() and (R4 == R).all()
+    assert (S.unpack(R4, m, n)[3] == g["ROW_AFTER"]).all()
+
+
 def test_rref_special_matrices():
     n = 20
     I = np.eye(n, dtype=np.uint8)
@@ -387,6 +423,11 @@ MUTANTS = {
     "mul_noacc": ("if (!acc)\n            memset", "if (1)\n            memset"),
     # MakeTable1 without the a-priori id fix
     "no_fix": ("    if (fix) {\n        for (int64_t i = 1; i < N; ++i) {", "    if (0) {\n        for (int64_t i = 1; i < N; ++i) {"),
+    # M4RI clearing only the rows below the block (an echelon form, not the reduced one)
+    "m4ri_below_only": ("vadd_rows_from_table(V, 0, r, c, kbar, T, L);", "(void)0;"),
+    # GaussSubmatrix without clearing above its pivots (the block is not the identity)
+    "gauss_submatrix_no_above": ("for (int64_t l = r; l < rs; ++l)\n                    if (vget(A, l, j))",
+                                 "for (int64_t l = rs; l < rs; ++l)\n                    if (vget(A, l, j))"),
 }
 
 
@@ -411,7 +452,8 @@ def _pins_pass(lib) -> bool:
     lib.gf2o_rref.restype = ctypes.c_int64
     lib.gf2o_pls_mmpf.restype = ctypes.c_int64
     lib.gf2o_pls_rec.restype = ctypes.c_int64
-    for f in ("gf2o_pls", "gf2o_rref", "gf2o_mul", "gf2o_pls_mmpf", "gf2o_pls_rec",
+    lib.gf2o_m4ri.restype = ctypes.c_int64
+    for f in ("gf2o_pls", "gf2o_rref", "gf2o_mul", "gf2o_pls_mmpf", "gf2o_pls_rec", "gf2o_m4ri",
               "gf2o_make_table", "gf2o_add_rows_from_table"):
         getattr(lib, f).argtypes = getattr(oracle._load(), f).argtypes
     oracle._lib = lib
@@ -422,6 +464,7 @@ def _pins_pass(lib) -> bool:
             test_pls_reconstruction_and_shape(kind)
             test_pls_matches_independent_restatement(kind)
         test_rref_unique_idempotent_structured("dense")
+        test_m4ri_reaches_the_unique_rref("dense")
         test_rank_brute_force_span()
         return True
     except AssertionError:
