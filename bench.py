@@ -1,13 +1,18 @@
 #!/usr/bin/env python3
-"""Benchmark: PLS + rank, plus RREF, of a 16384 x 16384 dense GF(2) matrix.
+"""Benchmark: PLS + rank of a 65536 x 65536 dense GF(2) matrix (the headline).
 
-One step = gf2_pls (PLS decomposition and rank, in place) and gf2_rref (the
-same matrix through the reduced-row-echelon route) on copies of a matrix that
-is already resident in HBM; the copies are restored at the start of each step.
-L2 (129 MB) is flushed between timed steps by writing a 256 MB buffer; the
-per-step device time excludes that flush.
+One step = gf2_pls (PLS decomposition and rank, in place, MMPF panels with
+XOR-table sweeps) on a matrix that is already resident in HBM; the matrix is
+restored from a pristine copy before each step, outside the timed events. The
+512 MB input is larger than L2 (129 MB), so no extra flush is needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gf2|reference]
+                  [--config 1|2|3|4|5] [--variants]
+
+--config 3 (default) is the headline line above; --config 3 --variants times
+the three 65536^2 matrices (dense, A = B.C, Bernoulli(0.01)) through MMPF and
+the recursive PLS with both products; --config 2 and 1 time 16384^2 and 1024^2
+PLS + RREF; --config 4 the 2048-matrix batch; --config 5 the request stream.
 
 Prints one JSON line (rank 0). Under torchrun (N > 1) every rank eliminates its
 own matrix (replicas: the elimination of one matrix has no data-parallel
@@ -29,10 +34,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "seconds per PLS+rank of n×n dense GF(2); effective bit-op/s, % of roofline"
-N_DEFAULT = 16384
 SEED = 0x10061744
-PAPER_CONTEXT = {"value_s": 3.388, "machine": "2.33 GHz Xeon E5345 (CPU)",
-                 "what": "PLS + RREF from PLS, random dense n=16384, Table 1", "note": "context only"}
+PAPER_CONTEXT = {"value_s": 151.314, "machine": "2.33 GHz Xeon E5345 (CPU)",
+                 "what": "PLS + RREF from PLS, random dense n = 64000 (the nearest to 65536), Table 1",
+                 "note": "context only: another machine, and it includes the RREF"}
 
 
 def effective_bitops(m: int, n: int, r: int) -> float:
@@ -50,11 +55,12 @@ def peaks():
 
 
 def traffic_from_profiles(name: str):
-    """DRAM bytes per launch of `name` recorded from an ncu capture in profiles/."""
+    """DRAM bytes over algorithmic bytes of one ncu-captured launch of a kernel, as recorded in
+    profiles/<name>.md (a line "traffic_ratio: X"); None if there is no such capture."""
     path = os.path.join(ROOT, "profiles", f"{name}.md")
     try:
         for line in open(path):
-            if line.startswith("traffic_bytes_per_launch:"):
+            if line.startswith("traffic_ratio:"):
                 v = line.split(":", 1)[1].strip()
                 return None if v in ("", "null") else float(v)
     except OSError:
@@ -114,39 +120,81 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_sample(n: int):
-    """The oracle as it stands (single-threaded C): Gaussian PLS + Gauss-Jordan RREF of one matrix."""
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_oracle_seconds(n: int, rref: bool = False, omp: bool = False) -> float:
+    """The oracle as it stands: Gaussian PLS (plus Gauss-Jordan RREF when rref) of one n x n matrix.
+    omp: the same PLS with the rows of each step spread over all host threads."""
     import oracle
     from paper_1006_1744_gb300 import synth
     A = synth.dense(n, n, SEED)
     t0 = time.perf_counter()
-    oracle.pls(A, n, n)
-    oracle.rref(A, n, n)
+    (oracle.pls_omp if omp else oracle.pls)(A, n, n)
+    if rref:
+        oracle.rref(A, n, n)
     return time.perf_counter() - t0
 
 
+def cpu_baseline(n: int, rref: bool):
+    """Single-thread oracle (the oracle of record) on a bounded sample, scaled to n x n by the
+    cubic cost, plus the all-cores OpenMP timing of the same sample."""
+    ns = min(n, 16384)
+    scale = (n / ns) ** 3
+    secs = cpu_oracle_seconds(ns, rref)
+    what = "Gaussian PLS" + (" + Gauss-Jordan RREF" if rref else "")
+    out = {"value": secs * scale, "unit": "s", "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
+           "sample": f"one {ns}x{ns} dense matrix: {what} (C oracle, single thread), {secs:.2f} s, "
+                     f"x {scale:g} for the cubic cost at {n}x{n}"}
+    if not rref:
+        try:
+            threads = os.cpu_count() or 1
+            so = cpu_oracle_seconds(ns, False, omp=True)
+            out["all_cores"] = {"value": so * scale, "unit": "s", "cores": threads, "kind": "oracle (OpenMP over "
+                                "the rows of each pivot step)", "sample_s": so, "sample": f"the same {ns}x{ns} PLS"}
+        except Exception as exc:  # no OpenMP runtime on this host
+            out["all_cores"] = {"unavailable": str(exc)[:200]}
+    return out
+
+
 def run_reference(args):
-    """Reference arm: the CPU oracle timed on the host cores."""
+    """Reference arm: the CPU oracle timed on the host cores, on the headline workload
+    (seconds per PLS + rank of a dense n x n matrix). Each step is one bounded sample: the
+    oracle's Gaussian PLS of an 8192 x 8192 dense matrix (single thread); its time is scaled by
+    (n / 8192)^3, the cubic cost, to the metric's unit. ms_per_step is the sample's own time."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    n = args.n
-    ns = min(n, 4096)  # bounded sample per step; time scaled by (n/ns)^3 (cubic elimination)
+    n = args.n or (65536 if args.config == 3 else 16384 if args.config == 2 else 1024)
+    ns = min(n, 8192)
     scale = (n / ns) ** 3
     for _ in range(args.warmup):
-        cpu_oracle_sample(ns)
-    times = [cpu_oracle_sample(ns) * scale for _ in range(args.steps)]
-    v = sum(times) / len(times)
+        cpu_oracle_seconds(ns)
+    t0 = time.perf_counter()
+    times = [cpu_oracle_seconds(ns) for _ in range(args.steps)]
+    wall = time.perf_counter() - t0
+    sample_s = sum(times) / len(times)
+    v = sample_s * scale
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": sample_s * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": f"{n}x{n} dense Bernoulli(1/2) GF(2): PLS + rank, plus RREF", "m": n, "n": n,
-                   "seed": SEED},
-        "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-                         "sample": f"per step one {ns}x{ns} matrix (Gaussian PLS + Gauss-Jordan RREF, single "
-                                   f"thread), time x {scale:g} for the cubic cost at {n}x{n}"},
+        "config": {"workload": f"{n}x{n} dense Bernoulli(1/2) GF(2): PLS + rank", "m": n, "n": n, "seed": SEED},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
+                         "sample": f"per step one {ns}x{ns} dense matrix (Gaussian PLS, C oracle, single thread; "
+                                   f"ms_per_step is that sample's time); value = sample x {scale:g} for the cubic "
+                                   f"cost at {n}x{n}"},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s_timed_region": wall,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -460,32 +508,48 @@ def run_config5(args):
     return 0
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="gf2", choices=["gf2", "reference"])
-    ap.add_argument("--n", type=int, default=N_DEFAULT)
-    ap.add_argument("--tile-words", type=int, default=0)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--config", type=int, default=2, choices=[2, 3, 4, 5],
-                    help="2: the headline line (default); 3: 65536^2 matrices, MMPF vs recursive PLS with "
-                         "XOR-table and tensor-core products; 4: batched PLS of 2048 matrices; 5: a stream of "
-                         "requests with Poisson arrivals, batched as they arrive")
-    ap.add_argument("--requests", type=int, default=4096, help="config 5: requests per arrival rate")
-    args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.config == 3:
-        return run_config3(args)
-    if args.config == 4:
-        return run_config4(args)
-    if args.config == 5:
-        return run_config5(args)
+def sweep_algorithmic_bytes(Q, m: int, W: int, r: int) -> float:
+    """Read + write bytes of the trailing blocks of all panels: panel b sweeps the (m - r_b) x (W - b)
+    trailing words, r_b = pivots left of column 64 b ((m - r)(n - c)/4 per panel)."""
+    import numpy as np
+    rb = np.searchsorted(np.asarray(Q[:r]), 64 * np.arange(W))
+    return float(np.sum((m - rb).clip(min=0) * (W - np.arange(W)) * 16.0))
 
+
+def side_numbers_16384(g, dev, steps: int):
+    """16384^2 figures kept beside the headline: gf2_pls, and gf2_rref by the PLS route, by
+    Algorithm M4RI and by the hybrid (CUDA events, L2 flushed before each call)."""
+    import torch
+    from paper_1006_1744_gb300 import synth_gpu
+    n = 16384
+    A0 = torch.empty((n, 256), dtype=torch.int64, device=dev)
+    synth_gpu.fill(A0, n, SEED)
+    A = torch.empty_like(A0)
+    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.int64, device=dev)
+    rk = torch.empty(1, dtype=torch.int64, device=dev)
+    piv = torch.empty(n, dtype=torch.int64, device=dev)
+    P = torch.empty(n, dtype=torch.int64, device=dev)
+    Q = torch.empty(n, dtype=torch.int64, device=dev)
+    wp = g.new_workspace(g.OP_PLS, n, n, device=dev)
+    wr = g.new_workspace(g.OP_RREF, n, n, device=dev)
+
+    def pre():
+        A.copy_(A0)
+        flush.zero_()
+
+    out = {"pls_s": _timed(lambda: g.pls(A, n, P=P, Q=Q, rank=rk, work=wp), steps, 3, pre) / 1e3}
+    for name, meth in (("rref_pls_route_s", g.RREF_PLS), ("rref_m4ri_s", g.RREF_M4RI),
+                       ("rref_hybrid_s", g.RREF_HYBRID)):
+        out[name] = _timed(lambda: g.rref(A, n, rank=rk, pivots=piv, work=wr, opts={"rref_method": meth}),
+                           steps, 3, pre) / 1e3
+    out["rank"] = int(rk.item())
+    out["note"] = "16384^2 dense (32 MB, L2-resident within a call); CUDA events; L2 flushed before each call"
+    return out
+
+
+def run_headline(args):
+    """PLS + rank of a dense n x n matrix (config 3: n = 65536, the headline), or PLS + RREF
+    (configs 2 and 1: n = 16384, 1024)."""
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -500,53 +564,44 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    n = m = args.n
+    n = m = args.n or {1: 1024, 2: 16384, 3: 65536}[args.config]
+    with_rref = args.config in (1, 2)
     W = (n + 63) // 64
     stride = max(16, (W + 15) // 16 * 16)
     opts = {"tile_words": args.tile_words} if args.tile_words else None
+    big = m * stride * 8 > 256 * 1024 * 1024  # input larger than L2: no flush needed
 
     A0 = torch.empty((m, stride), dtype=torch.int64, device=dev)
     synth_gpu.fill(A0, n, SEED + rank)
     A1 = torch.empty_like(A0)
-    A2 = torch.empty_like(A0)
+    A2 = torch.empty_like(A0) if with_rref else None
     wp = gf2.new_workspace(gf2.OP_PLS, m, n, device=dev)
-    wr = gf2.new_workspace(gf2.OP_RREF, m, n, device=dev)
+    wr = gf2.new_workspace(gf2.OP_RREF, m, n, device=dev) if with_rref else None
     P = torch.empty(m, dtype=torch.int64, device=dev)
     Q = torch.empty(n, dtype=torch.int64, device=dev)
     r1 = torch.empty(1, dtype=torch.int64, device=dev)
     r2 = torch.empty(1, dtype=torch.int64, device=dev)
     piv = torch.empty(n, dtype=torch.int64, device=dev)
-    flush = torch.empty(256 * 1024 * 1024 // 8, dtype=torch.int64, device=dev)
-    stream = torch.cuda.current_stream()
+    flush = None if big else torch.empty(256 * 1024 * 1024 // 8, dtype=torch.int64, device=dev)
+
+    def restore():
+        A1.copy_(A0)
+        if with_rref:
+            A2.copy_(A0)
+        if flush is not None:
+            flush.zero_()
 
     def step():
-        A1.copy_(A0)
-        A2.copy_(A0)
         gf2.pls(A1, n, P=P, Q=Q, rank=r1, work=wp, opts=opts)
-        gf2.rref(A2, n, rank=r2, pivots=piv, work=wr, opts=opts)
+        if with_rref:
+            gf2.rref(A2, n, rank=r2, pivots=piv, work=wr, opts=opts)
 
     for _ in range(args.warmup):
-        flush.zero_()
+        restore()
         step()
     torch.cuda.synchronize()
 
-    # separate timing of the two calls (one extra untimed step) for the breakdown
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    flush.zero_()
-    A1.copy_(A0)
-    A2.copy_(A0)
-    ev[0].record()
-    gf2.pls(A1, n, P=P, Q=Q, rank=r1, work=wp, opts=opts)
-    ev[1].record()
-    flush.zero_()
-    ev[2].record()
-    gf2.rref(A2, n, rank=r2, pivots=piv, work=wr, opts=opts)
-    ev[3].record()
-    torch.cuda.synchronize()
-    pls_ms = ev[0].elapsed_time(ev[1])
-    rref_ms = ev[2].elapsed_time(ev[3])
-
-    # ---- timed region (launches counted on the host, no events inside the steps) -------
+    # ---- timed region: restore (untimed) then the step between two events --------------
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     gf2.prof_reset()
@@ -558,7 +613,7 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(args.steps):
-        flush.zero_()
+        restore()
         starts[i].record()
         step()
         ends[i].record()
@@ -568,16 +623,16 @@ def main():
         dist.barrier()
     gf2.prof_enable(0)
     clocks = sampler.stop()
-    step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
+    step_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / args.steps
     launches = gf2.prof_launches()
 
-    # ---- per-kernel-class times: separate untimed steps with an event pair around each
-    # launch of the timed classes, on the stream it runs on ----------------------------
-    prof_steps = 3
+    # ---- per-kernel-class times: untimed steps with an event pair around each launch of the
+    # timed classes, on the stream it runs on ----------------------------------------------
+    prof_steps = 1 if n >= 32768 else 3
     gf2.prof_reset()
     gf2.prof_enable(3)
     for _ in range(prof_steps):
-        flush.zero_()
+        restore()
         step()
     torch.cuda.synchronize()
     gf2.prof_enable(0)
@@ -587,46 +642,46 @@ def main():
     gf2.prof_reset()
 
     step_ms_max = max_over_ranks(step_ms, world, dev)
-
     rank_val = int(r1.item())
-    assert rank_val == int(r2.item())
-    # algorithmic bytes of the table sweeps: panel b reads and writes the (m - r_b) x (W - b)
-    # trailing words (the panel word included); r_b = pivots left of column 64 b
-    q = Q[:rank_val].cpu().numpy()
-    rb = np.searchsorted(q, 64 * np.arange(W))
-    sweep_bytes_one = float(np.sum((m - rb).clip(min=0) * (W - np.arange(W)) * 16.0))
-    sweep_bytes = 2 * sweep_bytes_one * prof_steps  # both calls run the elimination
+    if with_rref:
+        assert rank_val == int(r2.item())
+    elims = 2 if with_rref else 1  # gf2_rref's PLS route runs the elimination too
+    sweep_bytes = sweep_algorithmic_bytes(Q.cpu().numpy(), m, W, rank_val) * elims * prof_steps
     hbm, peak_kind = peaks()
     shares = {"sweep": sweep_ms, "pivot": pivot_ms, "rref_block": rref_blk_ms}
     tot = sum(shares.values()) or 1.0
     dominant = max(shares, key=shares.get)
     achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9 if sweep_ms > 0 else 0.0
-    roofline = {"kernel": "k_sweep (table sweep: MakeTable1 + AddRowsFromTable)", "bound": "hbm",
+    bytes_per_launch = sweep_bytes / max(sweep_n, 1)
+    prof_name = f"k_sweep16_{n}"
+    traffic_ratio = traffic_from_profiles(prof_name)
+    roofline = {"kernel": "k_sweep16 (table sweep: MakeTable1 + AddRowsFromTable)", "bound": "hbm",
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
-                "traffic": traffic_from_profiles("k_sweep_16384"),
-                "algorithmic_bytes_per_launch": sweep_bytes / max(sweep_n, 1),
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst)" if peak_kind == "measured"
+                else peak_kind,
+                "traffic": traffic_ratio * bytes_per_launch if traffic_ratio else None,
+                "traffic_note": f"DRAM bytes / algorithmic bytes of one captured launch (profiles/{prof_name}.md) "
+                                "x the average launch's algorithmic bytes" if traffic_ratio else "no capture",
+                "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_us": sweep_ms * 1e3 / max(sweep_n, 1),
-                "note": "16384^2 packed is 32 MB and stays in the 129 MB L2 within a step"}
-
-    # the pivot search is one warp's dependent chain, not a bandwidth kernel: report it
-    # against the floor of that chain, one warp min-reduction (26 cycles) plus one 64-bit
-    # shuffle (38 cycles) per pivot at the SM clock (latencies measured on GB300 with a
-    # dependent-chain probe), 64 pivots per panel
+                "note": "bytes per panel = (m - r_b)(W - b) x 16 (read + write of the trailing words); "
+                        + ("the matrix is L2-resident within a step" if not big else "input larger than L2")}
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     pivot_us = pivot_ms * 1e3 / max(pivot_n, 1)
     floor_us = 64 * (26 + 38) / sm_mhz
     pivot_chain = {"kernel": "k_pivot (panel pivot search: PlsSubmatrix)", "bound": "latency",
-                   "avg_launch_us": pivot_us, "chain_floor_us": floor_us, "frac": floor_us / pivot_us if pivot_us else 0.0,
-                   "note": "1 CTA; the elimination chain of 64 pivots, plus window formation and the inverses"}
+                   "avg_launch_us": pivot_us, "chain_floor_us": floor_us,
+                   "frac": floor_us / pivot_us if pivot_us else 0.0,
+                   "note": "1 CTA; the elimination chain of 64 pivots (warp min-reduction 26 cycles + 64-bit "
+                           "shuffle 38 cycles per pivot), plus window formation and the inverses"}
 
-    # ---- end to end: host buffers, copies inside the timed region ---------------------
+    # ---- end to end through the C ABI: pinned host buffers, copies inside the timed region ---
     e2e = None
     if not args.no_e2e:
         hA = torch.empty((m, stride), dtype=torch.int64, pin_memory=True)
         hA.copy_(A0.cpu())
         hOut1 = torch.empty_like(hA, pin_memory=True)
-        hOut2 = torch.empty_like(hA, pin_memory=True)
+        hOut2 = torch.empty_like(hA, pin_memory=True) if with_rref else None
         hP = torch.empty(m, dtype=torch.int64, pin_memory=True)
         hQ = torch.empty(n, dtype=torch.int64, pin_memory=True)
         hpiv = torch.empty(n, dtype=torch.int64, pin_memory=True)
@@ -634,63 +689,102 @@ def main():
 
         def e2e_step():
             A1.copy_(hA, non_blocking=True)
-            A2.copy_(A1)
-            gf2.pls(A1, n, P=P, Q=Q, rank=r1, work=wp, opts=opts)
-            gf2.rref(A2, n, rank=r2, pivots=piv, work=wr, opts=opts)
+            if with_rref:
+                A2.copy_(A1)
+            step()
             hOut1.copy_(A1, non_blocking=True)
-            hOut2.copy_(A2, non_blocking=True)
             hP.copy_(P, non_blocking=True)
             hQ.copy_(Q, non_blocking=True)
-            hpiv.copy_(piv, non_blocking=True)
             hr[0:1].copy_(r1, non_blocking=True)
-            hr[1:2].copy_(r2, non_blocking=True)
+            if with_rref:
+                hOut2.copy_(A2, non_blocking=True)
+                hpiv.copy_(piv, non_blocking=True)
+                hr[1:2].copy_(r2, non_blocking=True)
 
         e2e_step()
         torch.cuda.synchronize()
+        e2e_steps = max(3, min(args.steps, 10))
         es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if world > 1:
             dist.barrier()
         es.record()
-        for _ in range(args.steps):
+        for _ in range(e2e_steps):
             e2e_step()
         ee.record()
         torch.cuda.synchronize()
-        te_ms = max_over_ranks(es.elapsed_time(ee) / args.steps, world, dev)
+        te_ms = max_over_ranks(es.elapsed_time(ee) / e2e_steps, world, dev)
         bi = m * stride * 8
-        bo = 2 * m * stride * 8 + (m + 2 * n + 2) * 8
+        bo = m * stride * 8 + (m + n + 1) * 8 + ((m * stride * 8 + n * 8 + 8) if with_rref else 0)
         e2e = {"value": job_seconds_per_matrix(te_ms, world), "unit": "s", "h2d_bytes_per_step": bi,
-               "d2h_bytes_per_step": bo, "ms_per_step": te_ms}
+               "d2h_bytes_per_step": bo, "ms_per_step": te_ms, "steps": e2e_steps}
+
+    side = None
+    if args.config == 3 and not args.no_side:
+        side = side_numbers_16384(gf2, dev, 10)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        secs = cpu_oracle_sample(n)
-        cpu = {"value": secs, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": f"one full {n}x{n} matrix: Gaussian PLS + Gauss-Jordan RREF (C oracle, single thread)"}
+        cpu = cpu_baseline(n, with_rref)
 
     if world > 1:
         dist.destroy_process_group()
     if rank != 0:
         return 0
     value = job_seconds_per_matrix(step_ms_max, world)
+    what = "PLS + rank" if not with_rref else "PLS + rank, plus the same matrix through gf2_rref"
     line = {
         "metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": f"{n}x{n} dense Bernoulli(1/2) GF(2): MMPF-style PLS + rank with XOR-table "
-                               f"trailing updates (k = 8), plus the same matrix through gf2_rref",
+        "config": {"workload": f"{n}x{n} dense Bernoulli(1/2) GF(2): {what}; MMPF panels with XOR-table "
+                               f"sweeps (k = 8 per table, 64 pivots per sweep)",
                    "m": m, "n": n, "seed": SEED, "parallelism": f"replicas x{world}",
-                   "l2": "flushed between timed steps (256 MB write, excluded from the step time)"},
-        "pls_s": pls_ms / 1e3, "rref_s": rref_ms / 1e3, "rank": rank_val,
-        "bitops_per_s": effective_bitops(m, n, rank_val) / (pls_ms / 1e3),
+                   "l2": ("input (512 MB) larger than L2; restored from a pristine copy before each step, "
+                          "outside the timed events") if big else
+                         "flushed between timed steps (256 MB write, excluded from the step time)"},
+        "rank": rank_val,
+        "bitops_per_s": effective_bitops(m, n, rank_val) / (step_ms_max / 1e3 / (elims if with_rref else 1)),
         "wall_s_timed_region": wall,
         "roofline": roofline, "pivot_chain": pivot_chain,
         "kernel_time_shares": {k: v / tot for k, v in shares.items()}, "dominant_kernel": dominant,
-        "kernel_launches": {"sweep": sweep_n, "pivot": pivot_n, "rref_block": rref_blk_n},
+        "kernel_launches": {"sweep": sweep_n, "pivot": pivot_n, "rref_block": rref_blk_n, "steps": prof_steps},
         "gpu_launches": launches,
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "paper_context": PAPER_CONTEXT,
     }
+    if side:
+        line["config2_16384"] = side
     print(json.dumps(line), flush=True)
     return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gf2", choices=["gf2", "reference"])
+    ap.add_argument("--n", type=int, default=0, help="matrix size of the headline form (default: by config)")
+    ap.add_argument("--tile-words", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-side", action="store_true", help="config 3: skip the 16384^2 side figures")
+    ap.add_argument("--config", type=int, default=3, choices=[1, 2, 3, 4, 5],
+                    help="3: 65536^2 PLS + rank (the headline, default); 2 / 1: 16384^2 / 1024^2 PLS + RREF; "
+                         "4: batched PLS of 2048 matrices; 5: a stream of requests with Poisson arrivals")
+    ap.add_argument("--variants", action="store_true",
+                    help="config 3: the three 65536^2 matrices through MMPF and the recursive PLS")
+    ap.add_argument("--requests", type=int, default=4096, help="config 5: requests per arrival rate")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.config == 3 and args.variants:
+        return run_config3(args)
+    if args.config == 4:
+        return run_config4(args)
+    if args.config == 5:
+        return run_config5(args)
+    return run_headline(args)
 
 
 if __name__ == "__main__":

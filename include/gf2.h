@@ -86,8 +86,18 @@ typedef struct gf2_opts {
     int product;        /* GF2_PRODUCT_*; used by gf2_mul */
     int64_t cutoff_cols;/* recursive PLS: MMPF base case at or below this many columns (Sec. 6); 0 = MMPF only.
                            Strassen products: the smallest dimension recursed on (0 = 8192) */
-    int reserved[8];    /* must be zero */
+    int rref_method;    /* gf2_rref: GF2_RREF_* (0 = GF2_RREF_AUTO) */
+    int hybrid_permille;/* GF2_RREF_HYBRID: switch to PLS once the remaining rows' density reaches this many
+                           per mille (Sec. 6, "M+P 0.15"; 0 = 150) */
+    int reserved[6];    /* must be zero */
 } gf2_opts;
+
+/* routes of gf2_rref (all reach the same, unique, reduced row echelon form) */
+#define GF2_RREF_AUTO 0   /* the library's choice (currently GF2_RREF_PLS) */
+#define GF2_RREF_PLS 1    /* PLS decomposition, then the upper solve (Table 1's "PLS" column) */
+#define GF2_RREF_M4RI 2   /* Algorithm M4RI (Sec. 3.1): each panel's tables clear the rows above and below */
+#define GF2_RREF_HYBRID 3 /* "M+P" (Sec. 6-7): M4RI panels while the remaining rows are sparse, then PLS panels
+                             and the upper solve over the PLS panels' pivots only */
 
 /*
  * Bytes of workspace an operation needs for an m x n matrix. For GF2_OP_MUL
@@ -128,9 +138,18 @@ int gf2_pls(uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *P, int64
             void *work, size_t work_bytes, const gf2_opts *opts, void *stream);
 
 /*
- * Reduced row echelon form, in place (Definition "Reduced Row Echelon Form";
- * the PLS route of Table 1: PLS decomposition, then R = (S restricted to its
- * pivot columns)^-1 . S by an upper-triangular solve over 64-pivot blocks).
+ * Reduced row echelon form, in place (Definition "Reduced Row Echelon Form").
+ * opts->rref_method picks the route; all give the same (unique) result:
+ *   GF2_RREF_PLS (default): the PLS route of Table 1: PLS decomposition, then
+ *     R = (S restricted to its pivot columns)^-1 . S by an upper-triangular
+ *     solve over 64-pivot blocks;
+ *   GF2_RREF_M4RI: Algorithm M4RI (Sec. 3.1): every 64-column panel's pivot
+ *     search, then one table sweep that clears the panel's pivot columns in
+ *     every other row, above and below;
+ *   GF2_RREF_HYBRID: M4RI sweeps while the density of the remaining rows (the
+ *     set bits of their next panel word, counted by each sweep) stays below
+ *     opts->hybrid_permille, PLS sweeps from then on, then the upper solve
+ *     over the pivots found after the switch (Sec. 6, "M+P").
  * On return rows [0, r) of A hold the RREF and rows [r, m) are zero.
  *   pivots -- device int64, length n, nullable: pivots[i] = column of the
  *             leading 1 of row i for i < r (the column rank profile), i for i >= r;

@@ -62,6 +62,9 @@ ElimLayout elim_layout(int op, int64_t m, int64_t n)
         L.rref_d = off;
         off = align_up(off + (size_t)((m + 63) / 64 + 1) * 64 * sizeof(u64), 256);
     }
+    L.ups = off;
+    if (op == GF2_OP_RREF)
+        off = align_up(off + (size_t)2 * m * sizeof(u64), 256);
     // int64 Q scratch for rref (length n)
     off = align_up(off + (size_t)(n + 1) * sizeof(int64_t), 256);
     L.total = off;
@@ -151,7 +154,9 @@ int check_opts(const gf2_opts *o)
         return GF2_EINVAL;
     if (o->cutoff_cols != 0 && o->cutoff_cols < 128)
         return GF2_EINVAL;
-    for (int i = 0; i < 8; ++i)
+    if (o->rref_method < 0 || o->rref_method > GF2_RREF_HYBRID || o->hybrid_permille < 0 || o->hybrid_permille > 1000)
+        return GF2_EINVAL;
+    for (int i = 0; i < 6; ++i)
         if (o->reserved[i])
             return GF2_EINVAL;
     return GF2_OK;
@@ -172,11 +177,14 @@ static Elim make_elim(uint64_t *A, int64_t m, int64_t n, int64_t stride, char *w
     e.side = reinterpret_cast<u64 *>(work + L.side);
     e.pmask = reinterpret_cast<u64 *>(work + L.pmask);
     e.out = with_out ? reinterpret_cast<uint64_t *>(work + L.out) : nullptr;
+    e.ups = nullptr;  // set by gf2_rref for the reduced form
     e.ostride = min_stride(n);
     e.P = P;
     e.Q = Q;
     e.s = s;
     e.tile_words = (o && o->tile_words) ? o->tile_words : 16;
+    e.mode = 0;
+    e.hybrid_permille = o ? o->hybrid_permille : 0;
     // default: one CTA per SM but one, so the look-ahead pivot search (which cannot share an
     // SM with a 1024-thread sweep CTA) never holds back a CTA of the sweep it overlaps
     const int nsm = sm_count();
@@ -319,14 +327,24 @@ int gf2_rref(uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *rank, i
         return rc;
     char *w = (char *)work;
     int64_t *Qs = reinterpret_cast<int64_t *>(w + q_scratch_offset(L, n));
-    const Elim e = make_elim(A, m, n, stride, w, L, nullptr, Qs, true, opts, s);
-    return run_replayed(call_key(GF2_OP_RREF, A, m, n, stride, nullptr, nullptr, rank, pivots, work, work_bytes, e),
-                        s, [&](cudaStream_t st) {
-                            Elim es = e;
-                            es.s = st;
-                            const int r2 = elim_run(es);
-                            return r2 ? r2 : rref_finish(es, L, w, rank, pivots);
-                        });
+    Elim e = make_elim(A, m, n, stride, w, L, nullptr, Qs, true, opts, s);
+    const int method = (opts && opts->rref_method) ? opts->rref_method : GF2_RREF_PLS;
+    // the sweep form: PLS panels (then the upper solve), reduced-form panels (M4RI), or the hybrid
+    e.mode = method == GF2_RREF_M4RI ? 1 : method == GF2_RREF_HYBRID ? 2 : 0;
+    e.ups = reinterpret_cast<u64 *>(w + L.ups);
+    if (e.mode && e.tile_words != 16)
+        return GF2_EINVAL;  // the reduced form is built on the 16-word sweep only
+    CallKey key = call_key(GF2_OP_RREF + 16 * e.mode, A, m, n, stride, nullptr, nullptr, rank, pivots, work,
+                           work_bytes, e);
+    key.grid += e.hybrid_permille << 16;  // the threshold changes the launches' behaviour
+    return run_replayed(key, s, [&](cudaStream_t st) {
+        Elim es = e;
+        es.s = st;
+        const int r2 = elim_run(es);
+        if (r2)
+            return r2;
+        return es.mode == 1 ? m4ri_finish(es, rank, pivots) : rref_finish(es, L, w, rank, pivots);
+    });
 }
 
 int gf2_rank(const uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *rank, void *work,

@@ -28,8 +28,10 @@ struct PanelState {
     int zero_tail;  // 1 once every remaining row is zero in every remaining column
     int nz;         // set by this panel's sweep when it found no pivot but a nonzero word right of
                     // the panel in a trailing row (checked only then)
-    int pad0[2];
+    int mode;       // form of this panel's sweep: 0 = PLS (trailing rows), 1 = reduced form (every row)
+    int r_switch;   // hybrid: rank before the first panel swept in PLS form (INT_MAX while none)
     u64 J;          // pivot columns of the panel, as a bit mask of the panel word
+    unsigned long long pop;  // hybrid: set bits of the trailing rows' next panel word, counted by this sweep
     int prow[64];   // physical row of pivot t (rows are never moved during elimination)
     int pcol[64];   // panel-relative column of pivot t
     u64 newblk[64]; // pivot t -> its final panel word (U_t plus its own multipliers)
@@ -104,6 +106,20 @@ __device__ __forceinline__ void gray16(u64 base, u64 r0, u64 r1, u64 r2, u64 r3,
         cur ^= k == 0 ? r0 : k == 1 ? r1 : k == 2 ? r2 : r3;
         T[(i ^ (i >> 1)) * ts] = cur;
     }
+}
+
+// Physical row at trailing position p >= r of the panel that st describes: its
+// window order, its swaps past the window, else perm (which the next panel's
+// pivot search may be rewriting meanwhile, at exactly those positions).
+__device__ __forceinline__ int trailing_row(const int *__restrict__ perm, const PanelState *__restrict__ st, int r,
+                                            int nwin, int nx, int p)
+{
+    if (p < r + nwin)
+        return st->wperm[p - r];
+    for (int x = 0; x < nx; ++x)
+        if (st->xpos[x] == p)
+            return st->xval[x];
+    return perm[p];
 }
 
 // ---------------------------------------------------------------------------
@@ -223,6 +239,7 @@ struct ElimLayout {
     size_t rref_b;  // rref: non-pivot part of S, compacted
     size_t rref_x;  // rref: solved non-pivot part
     size_t rref_d;  // rref: inverses of the 64x64 diagonal blocks
+    size_t ups;     // rref: u64[2][m]: panel word of each row above the panel, by position (double buffered)
     size_t total;
 };
 int64_t min_stride(int64_t n);
@@ -241,9 +258,13 @@ struct Elim {
     u64 *pmask;
     uint64_t *out;    // final-order rows (nullptr for rank)
     int64_t ostride;  // row pitch of out, words (minimal: ceil(n/64) rounded up to 16)
+    u64 *ups;         // reduced form: panel word of the rows above, by position, double buffered (2 x m)
     int64_t *P, *Q;   // nullable for rank
     cudaStream_t s;
     int tile_words, grid;
+    int mode;         // table sweeps: 0 = PLS (trailing rows), 1 = reduced echelon form (every row),
+                      // 2 = hybrid (reduced form until the density reaches hybrid_permille, then PLS)
+    int hybrid_permille;
 };
 
 // One matrix of a batched elimination (device-resident array, one per matrix).
@@ -269,6 +290,8 @@ int batch_sweep(const ElimDesc *D, const int *idx, const int *pre, int nact, int
                 cudaStream_t s);
 int batch_finish(const ElimDesc *D, int count, int max_m, cudaStream_t s);
 int sweep_rows_per_pass(int tile_words);
+// table sweep of panel b over 16-word tiles (gf2_sweep.cu), in the form e.mode selects
+int launch_sweep16(const Elim &e, int b, cudaStream_t s);
 int sweep_ctas_per_sm(int tile_words);
 
 // panel elimination: runs every panel; afterwards st->r_next is the rank.
@@ -290,6 +313,8 @@ int elim_gather(const Elim &e, int64_t *rank);
 int pls_finish(const Elim &e);
 // RREF from the eliminated rows in e.out, written into e.A
 int rref_finish(const Elim &e, const ElimLayout &L, char *work, int64_t *rank, int64_t *pivots);
+// RREF of an elimination in reduced form (e.mode 1): gather, copy back, pivots
+int m4ri_finish(const Elim &e, int64_t *rank, int64_t *pivots);
 // product
 int mul_xor(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64_t *B, int64_t sb,
             int64_t m, int64_t k, int64_t n, int acc, int tile_words, int grid, cudaStream_t s);

@@ -47,6 +47,9 @@ __global__ void k_init(const uint64_t *__restrict__ A, int64_t stride, int *__re
         st[i].zero_tail = 0;
         st[i].nz = 0;
         st[i].J = 0;
+        st[i].mode = 0;
+        st[i].r_switch = INT_MAX;
+        st[i].pop = 0;
     }
 }
 
@@ -583,7 +586,7 @@ static_assert(WIN <= PIVOT_THREADS, "one window row per thread when the window i
 __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int64_t stride,
                                             const u64 *__restrict__ side_prev, int *__restrict__ perm,
                                             const PanelState *__restrict__ st_prev, PanelState *st, int64_t *P,
-                                            int64_t *Q, int m, int b, int nbits)
+                                            int64_t *Q, int m, int b, int nbits, int form, int thr_permille)
 {
     __shared__ PivotShared S;
     __shared__ u64 sXp[64], sXm[64];
@@ -763,6 +766,23 @@ __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int6
         st->xmap[tid] = sXm[tid];
     }
     if (tid == 0) {
+        // form of this panel's sweep. Hybrid ("M+P", Sec. 6): the reduced form while the
+        // density of the remaining rows -- the set bits of word b - 1 that the sweep of panel
+        // b - 2 counted over its trailing rows -- stays below the threshold, PLS from then on.
+        // st still holds panel b - 2's state here.
+        int mode = form < 2 ? form : 1;
+        if (form == 2) {
+            const int prev = b > 0 ? st_prev->mode : 1;
+            const long long rows = (long long)m - st->r_next;
+            if (prev == 0)
+                mode = 0;
+            else if (b >= 2 && rows > 0 && (long long)st->pop * 1000 >= (long long)thr_permille * rows * 64)
+                mode = 0;
+        }
+        const int rsw_prev = b > 0 ? st_prev->r_switch : INT_MAX;
+        st->mode = mode;
+        st->r_switch = (mode == 0 && rsw_prev == INT_MAX) ? r : rsw_prev;
+        st->pop = 0;
         st->r_cur = r;
         st->kbar = t;
         st->r_next = r + t;
@@ -791,11 +811,12 @@ __global__ void k_apply_order(int *__restrict__ perm, const PanelState *__restri
 // are visible. Without the launch attribute both instructions are no-ops.
 __global__ void __launch_bounds__(PIVOT_THREADS, 1)
 k_pivot(const uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_prev, int *__restrict__ perm,
-        const PanelState *__restrict__ st_prev, PanelState *st, int64_t *P, int64_t *Q, int m, int b, int nbits)
+        const PanelState *__restrict__ st_prev, PanelState *st, int64_t *P, int64_t *Q, int m, int b, int nbits,
+        int form, int thr_permille)
 {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    pivot_panel(A, stride, side_prev, perm, st_prev, st, P, Q, m, b, nbits);
+    pivot_panel(A, stride, side_prev, perm, st_prev, st, P, Q, m, b, nbits, form, thr_permille);
 }
 
 // ---------------------------------------------------------------------------
@@ -816,20 +837,6 @@ k_pivot(const uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ 
 // CTA takes an equal contiguous run of that tile-major sequence, builds a tile's
 // tables once per tile it meets, and keeps RPT rows per thread in flight.
 // ---------------------------------------------------------------------------
-// physical row at trailing position p of the panel that st describes: its
-// window order, its swaps past the window, else perm (which the next panel's
-// pivot search may be rewriting meanwhile, at exactly those positions)
-__device__ __forceinline__ int trailing_row(const int *__restrict__ perm, const PanelState *__restrict__ st, int r,
-                                            int nwin, int nx, int p)
-{
-    if (p < r + nwin)
-        return st->wperm[p - r];
-    for (int x = 0; x < nx; ++x)
-        if (st->xpos[x] == p)
-            return st->xval[x];
-    return perm[p];
-}
-
 // rows of one pass of the sweep: position -> physical row, pivot row or not, in range
 template <int RPT, int RPP>
 __device__ __forceinline__ void pass_rows(int pb, int rg, int p_end, int r, int kbar, int nwin, int nx,
@@ -1322,6 +1329,9 @@ __global__ void k_init_b(const gf2::ElimDesc *__restrict__ D)
         d.st[g].zero_tail = 0;
         d.st[g].nz = 0;
         d.st[g].J = 0;
+        d.st[g].mode = 0;
+        d.st[g].r_switch = 0;
+        d.st[g].pop = 0;
     }
 }
 
@@ -1330,7 +1340,7 @@ __global__ void __launch_bounds__(PIVOT_THREADS, 1) k_pivot_b(const gf2::ElimDes
     const gf2::ElimDesc &d = D[idx[blockIdx.x]];
     const int nbits = min(64, d.n - 64 * b);
     pivot_panel(d.A, d.stride, d.side + (size_t)((b + 1) & 1) * d.m, d.perm, d.st + ((b + 1) & 1), d.st + (b & 1),
-                d.P, d.Q, d.m, b, nbits);
+                d.P, d.Q, d.m, b, nbits, 0, 0);
 }
 
 template <int TW, int RPT, int NT, int MINB>
@@ -1583,8 +1593,9 @@ int elim_run(const Elim &e, const ElimAux &aux)
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             const PanelState *stp = e.st + ((b + 1) & 1);
+            const int thr = e.hybrid_permille > 0 ? e.hybrid_permille : 150;
             rc = note_cuda(cudaLaunchKernelEx(&cfg, k_pivot, (const uint64_t *)e.A, e.stride, prev, e.perm, stp, stb,
-                                              e.P, e.Q, m, b, nbits));
+                                              e.P, e.Q, m, b, nbits, e.mode, thr));
         }
         prof_end(e.s, GF2_PROF_PIVOT, tok);
         prof_launched(1);
@@ -1593,7 +1604,7 @@ int elim_run(const Elim &e, const ElimAux &aux)
             return rc;
         rc = e.tile_words == 4   ? launch_sweep<4, 1, 512, 2>(e, b, t)
              : e.tile_words == 8 ? launch_sweep<8, 1, 1024, 1>(e, b, t)
-                                 : launch_sweep<16, 1, 1024, 1>(e, b, t);
+                                 : launch_sweep16(e, b, t);
         if (rc || (rc = note_cuda(cudaEventRecord(ev_rest[b & 1], t))))
             return rc;
     }

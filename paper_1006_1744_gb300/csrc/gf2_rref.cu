@@ -148,6 +148,16 @@ k_rref_group(u64 *__restrict__ Bc, u64 *__restrict__ Xc, int64_t sb, const uint6
         return;
     const int rows = min(G * 64, r - base);
     const int qend = q0 + (rows + 63) / 64;  // one past the group's last block
+    if (64 * qend <= st->r_switch) {
+        // every row of the group was reduced by the hybrid's reduced-form panels: its diagonal
+        // blocks are the identity and it has no entries in its own blocks, so X = B
+        for (int e = tid; e < rows * TW1; e += blockDim.x) {
+            const int i = e / TW1, w = e % TW1;
+            if (wb + w < NB)
+                Xc[(int64_t)(base + i) * sb + wb + w] = Bc[(int64_t)(base + i) * sb + wb + w];
+        }
+        return;
+    }
     for (int e = tid; e < G * 64 * TW1; e += blockDim.x) {
         const int i = e / TW1, w = e % TW1;
         sB[e] = (i < rows && wb + w < NB) ? Bc[(int64_t)(base + i) * sb + wb + w] : 0ull;
@@ -208,6 +218,8 @@ k_rref_bulk(u64 *__restrict__ Bc, const u64 *__restrict__ Xc, int64_t sb, const 
         return;
     const int tid = threadIdx.x;
     const int nblk = min(G, (r - above + 63) / 64);
+    if (64 * (q0 + nblk) <= st->r_switch)
+        return;  // the group and every row above it were reduced by the hybrid's reduced-form panels
     const int tiles = (NB + TWG - 1) / TWG;
     int chunks = gridDim.x / tiles;
     if (chunks < 1)
@@ -324,6 +336,21 @@ __global__ void k_pmask2(const int64_t *__restrict__ Q, const PanelState *__rest
 }  // namespace
 
 namespace gf2 {
+
+// Algorithm M4RI's result: the pivot rows are already reduced (in `out`, final positions, words
+// from their panel on); the gather adds their zero words left of the panel and the zero rows
+// past the rank, then `out` is copied back. pivots = Q.
+int m4ri_finish(const Elim &e, int64_t *rank, int64_t *pivots)
+{
+    int rc = elim_gather(e, rank);
+    if (rc)
+        return rc;
+    cudaError_t err = cudaMemcpy2DAsync(e.A, (size_t)e.stride * 8, e.out, (size_t)e.ostride * 8, (size_t)e.W * 8,
+                                        (size_t)e.m, cudaMemcpyDeviceToDevice, e.s);
+    if (err == cudaSuccess && pivots)
+        err = cudaMemcpyAsync(pivots, e.Q, (size_t)e.n * sizeof(int64_t), cudaMemcpyDeviceToDevice, e.s);
+    return note_cuda(err);
+}
 
 int rref_finish(const Elim &e, const ElimLayout &L, char *work, int64_t *rank, int64_t *pivots)
 {

@@ -22,6 +22,7 @@ _lib = None
 
 OP_PLS, OP_RREF, OP_RANK, OP_MUL = 1, 2, 3, 4
 PRODUCT_AUTO, PRODUCT_XOR, PRODUCT_TENSOR, PRODUCT_STRASSEN, PRODUCT_STRASSEN_TENSOR = 0, 1, 2, 3, 4
+RREF_AUTO, RREF_PLS, RREF_M4RI, RREF_HYBRID = 0, 1, 2, 3
 
 _i64 = ctypes.c_int64
 _vp = ctypes.c_void_p
@@ -40,7 +41,7 @@ class Gf2Error(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("k", _int), ("tile_words", _int), ("grid_ctas", _int), ("product", _int),
-                ("cutoff_cols", _i64), ("reserved", _int * 8)]
+                ("cutoff_cols", _i64), ("rref_method", _int), ("hybrid_permille", _int), ("reserved", _int * 6)]
 
 
 class BatchItem(ctypes.Structure):
