@@ -89,8 +89,14 @@ typedef struct gf2_opts {
     int rref_method;    /* gf2_rref: GF2_RREF_* (0 = GF2_RREF_AUTO) */
     int hybrid_permille;/* GF2_RREF_HYBRID: switch to PLS once the remaining rows' density reaches this many
                            per mille (Sec. 6, "M+P 0.15"; 0 = 150) */
-    int reserved[6];    /* must be zero */
+    int batch_mode;     /* gf2_pls_batched: GF2_BATCH_* (0 = GF2_BATCH_AUTO) */
+    int reserved[5];    /* must be zero */
 } gf2_opts;
+
+/* schedules of gf2_pls_batched (same results) */
+#define GF2_BATCH_AUTO 0       /* persistent unless a member would need a team of more than 16 CTAs */
+#define GF2_BATCH_STEPS 1      /* two launches per panel step over all matrices that have that panel */
+#define GF2_BATCH_PERSISTENT 2 /* one persistent launch: teams of CTAs take whole matrices (16-word tiles only) */
 
 /* routes of gf2_rref (all reach the same, unique, reduced row echelon form) */
 #define GF2_RREF_AUTO 0   /* the library's choice (currently GF2_RREF_PLS) */
@@ -129,6 +135,10 @@ size_t gf2_mul_workspace_bytes(int64_t m, int64_t k, int64_t n, const gf2_opts *
  * [L_i in cols < i | 1 at col i | 0 up to col Q[i] | S_i right of Q[i] in its
  * original columns]; rows >= r hold only L. *rank = r. P, Q as above.
  * Identical, bit for bit, to the Gaussian PLS algorithm of the appendix.
+ * With opts->cutoff_cols > 0 and n above it, the recursive PLS of Sec. 5 runs
+ * instead; its trailing products are sized by the rank of each base case, so
+ * that route waits for `stream` (host-blocking) once per base case. The
+ * default (MMPF panels) never waits.
  *   A      -- device, m x n, stride words per row (layout above), in/out;
  *   P, Q   -- device int64, length m and n, out (may not alias A or work);
  *   rank   -- device int64, out.
@@ -184,8 +194,13 @@ int gf2_mul(uint64_t *C, int64_t sc, const uint64_t *A, int64_t sa, const uint64
 /*
  * Batched PLS: many independent matrices in one call (the paper decomposes one
  * matrix at a time; the batch runs the same MMPF block elimination, Sec. 4.1,
- * on every matrix at once, so that step b -- the pivot search and the table
- * sweep of panel b -- is one launch over all matrices that have a panel b).
+ * on every matrix). Two schedules (opts->batch_mode): GF2_BATCH_STEPS runs
+ * step b -- the pivot search and the table sweep of panel b -- as one launch
+ * over all matrices that have a panel b; GF2_BATCH_PERSISTENT runs the whole
+ * batch in one cooperative launch with one CTA per SM, where the largest
+ * matrices are eliminated by teams of CTAs (barriers between the pivot search
+ * and the sweep of each panel, bounded waits reporting GF2_ETIMEOUT) and the
+ * others one per CTA, taken from a device work queue.
  * Each matrix's results are bit for bit those of gf2_pls on it alone without
  * the recursive split (opts->cutoff_cols is ignored).
  *   items  -- HOST array of `count` descriptors; the pointers inside are device
@@ -268,7 +283,8 @@ int gf2_diag_wait_timeout(uint64_t limit_ns, void *stream);
  * allocates and frees its own device buffers. Candidates:
  *   GF2_OP_PLS / RREF / RANK: tile_words 4, 8 and 16; for PLS with n > 8192 also
  *     the recursive split at 4096 columns with the XOR-table and the
- *     tensor-core product;
+ *     tensor-core product; for RREF also the M4RI route and the hybrid at
+ *     150 and 200 per mille;
  *   GF2_OP_MUL (C = A.B with A m x n, B n x n): the XOR-table and the
  *     tensor-core product, and where a level applies (m, n >= 16384, n a
  *     multiple of 2048) Strassen-Winograd over either.

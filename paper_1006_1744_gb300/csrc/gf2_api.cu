@@ -156,7 +156,9 @@ int check_opts(const gf2_opts *o)
         return GF2_EINVAL;
     if (o->rref_method < 0 || o->rref_method > GF2_RREF_HYBRID || o->hybrid_permille < 0 || o->hybrid_permille > 1000)
         return GF2_EINVAL;
-    for (int i = 0; i < 6; ++i)
+    if (o->batch_mode < 0 || o->batch_mode > GF2_BATCH_PERSISTENT)
+        return GF2_EINVAL;
+    for (int i = 0; i < 5; ++i)
         if (o->reserved[i])
             return GF2_EINVAL;
     return GF2_OK;

@@ -289,9 +289,22 @@ int batch_pivot(const ElimDesc *D, const int *idx, int nact, int b, cudaStream_t
 int batch_sweep(const ElimDesc *D, const int *idx, const int *pre, int nact, int total, int b, int tile_words,
                 cudaStream_t s);
 int batch_finish(const ElimDesc *D, int count, int max_m, cudaStream_t s);
+// The whole batch in one persistent cooperative launch (one CTA per SM): team t < nteams (CTAs
+// team_start[t] .. + team_size[t]; team_of[cta] = its team or -1) takes the matrices
+// big[team_first[t] .. team_first[t + 1]), then every CTA takes the matrices small[0 .. nsmall)
+// from a work queue. All arrays are device memory; counters: nteams + 2 ints.
+struct PersistArrays {
+    const int *team_of, *team_start, *team_size, *team_first, *big, *small;
+};
+int batch_persistent(const ElimDesc *D, int nteams, const PersistArrays &a, int nsmall, int *counters,
+                     cudaStream_t s);
+int batch_persistent_grid();  // CTAs of that launch
 int sweep_rows_per_pass(int tile_words);
 // table sweep of panel b over 16-word tiles (gf2_sweep.cu), in the form e.mode selects
 int launch_sweep16(const Elim &e, int b, cudaStream_t s);
+// the same for panel b of a batch (PLS form), CTAs shared out as for batch_sweep
+int batch_sweep16(const ElimDesc *D, const int *idx, const int *pre, int nact, int total, int b, cudaStream_t s);
+constexpr int SWEEP16_ROWS = 128;  // rows per block of work of the 16-word sweep
 int sweep_ctas_per_sm(int tile_words);
 
 // panel elimination: runs every panel; afterwards st->r_next is the rank.

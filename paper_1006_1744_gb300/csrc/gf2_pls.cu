@@ -19,6 +19,7 @@
 #include <mutex>
 
 #include "gf2_common.cuh"
+#include "gf2_sweep.cuh"
 
 namespace {
 
@@ -575,6 +576,10 @@ __device__ void pivot_rows(const WordCtx &wc, const int *__restrict__ perm, int 
 }
 
 constexpr int PIVOT_THREADS = 128;  // warp 0 runs the elimination chain; all four share the rest
+
+// The pivot search's threads (the first PIVOT_THREADS of the CTA) synchronise on a named barrier of
+// their own, so that a larger CTA can run it while its other warps do something else.
+__device__ __forceinline__ void pivot_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(PIVOT_THREADS) : "memory"); }
 static_assert(WIN <= PIVOT_THREADS, "one window row per thread when the window is formed");
 
 // Pivot search of panel b. It first applies panel b - 1's row-order changes to
@@ -634,7 +639,7 @@ __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int6
     }
     if (tid == 0)
         S.nx = 0;
-    __syncthreads();
+    pivot_barrier();
     if (b > 0)
         for (int e = tid; e < 2 * 256; e += PIVOT_THREADS) {
             const int which = e >> 8, q = (e >> 4) & 15, vv = e & 15;
@@ -645,12 +650,12 @@ __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int6
                 x ^= ((vv >> bit) & 1) ? src[4 * q + bit] : 0ull;
             (which ? S.pNO : S.pNZ)[q][vv] = x;
         }
-    __syncthreads();
+    pivot_barrier();
     if (tid < nwin) {
         S.Wph[tid] = ph;
         S.Ww[tid] = b > 0 ? word_after(S, w, v) : w;
     }
-    __syncthreads();
+    pivot_barrier();
     if (warp == 0) {
         int t = 0, fast = 1;
         u64 J = 0;
@@ -669,7 +674,7 @@ __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int6
         sXp[tid - 32] = 0;
         sXm[tid - 32] = 0;
     }
-    __syncthreads();
+    pivot_barrier();
     const int t = sT;
     const u64 J = sJ;
     // Inverses, one column per lane: warps 2, 3 -> L^-1 (rows top-down: row s = e_s +
@@ -721,7 +726,7 @@ __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int6
                 dst[2 * (lane + 32) + (warp & 1)] = hi;
         }
     }
-    __syncthreads();
+    pivot_barrier();
     // maps for the sweep, by pivot column: row of M = U_J^-1 L^-1 (= (O_J)^-1: raw panel bits ->
     // coordinates over the original pivot rows) and the row of U_J^-1 scattered to the pivot
     // columns. Two threads per row of M, each over half of the inner index.
@@ -743,7 +748,7 @@ __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int6
             sXm[S.sPcol[row]] = pdep64(ua, J);
         }
     }
-    __syncthreads();
+    pivot_barrier();
     // row order of the window (applied to perm by the next panel), P and Q, the panel state
     for (int i = tid; i < nwin; i += PIVOT_THREADS)
         st->wperm[i] = S.Wph[i];
@@ -1403,6 +1408,155 @@ __global__ void k_copyback_b(const gf2::ElimDesc *__restrict__ D)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Batched elimination in one persistent launch (cooperative: every CTA is
+// resident). Teams of G CTAs eliminate one matrix at a time, panel by panel:
+// the pivot search of panel b (the first PIVOT_THREADS threads of the team's
+// first CTA), then the table sweep of panel b over all of the team's CTAs,
+// with a team barrier after each, then the finishing steps (row order, gather,
+// compression of L, copy back). The large matrices go to teams of CTAs (a
+// contiguous CTA range and a list of matrices per team, planned on the host);
+// every CTA then takes small matrices one at a time from a device work queue,
+// as a team of one.
+// ---------------------------------------------------------------------------
+struct PersistPlan {
+    int nteams;
+    const int *team_of;       // per CTA: its large-matrix team, or -1
+    const int *team_start;    // per team: its first CTA ...
+    const int *team_size;     // ... and its CTA count
+    const int *team_first;    // team t's matrices: big[team_first[t] .. team_first[t + 1])
+    const int *big;
+    const int *small;         // matrices for single CTAs, largest first
+    int nsmall;
+    int *next_small;          // work-queue cursor into small (zero at launch)
+    unsigned *bars;           // barrier counter of each team (zero at launch)
+    int *abort;               // set when a barrier wait gave up (zero at launch)
+    int *status;              // device status word
+};
+
+__device__ __forceinline__ unsigned ld_volatile(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.volatile.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// Barrier of the G CTAs of a team (a plain CTA barrier for G = 1). The wait is bounded: one that
+// gives up records GF2_ETIMEOUT and sets the abort flag, and every CTA then leaves.
+__device__ __forceinline__ bool team_barrier(unsigned *bar, unsigned &target, int G, const PersistPlan &pl)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (G == 1)
+        return true;
+    if (threadIdx.x == 0) {
+        target += (unsigned)G;
+        __threadfence();
+        atomicAdd(bar, 1u);
+        const u64 t0 = globaltimer_ns();
+        int ok = 1;
+        while (ld_volatile(bar) < target) {
+            if (*(volatile int *)pl.abort || globaltimer_ns() - t0 > GF2_WAIT_LIMIT_NS) {
+                if (!*(volatile int *)pl.abort)
+                    record_status(pl.status, GF2_ETIMEOUT);
+                atomicExch(pl.abort, 1);
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// The whole MMPF elimination of one matrix by CTA tr of a team of G.
+__device__ bool team_eliminate(SweepSmem &S, const gf2::ElimDesc &d, int tr, int G, unsigned *bar, unsigned &target,
+                               const PersistPlan &pl)
+{
+    const int tid = threadIdx.x;
+    const int m = d.m, W = d.W;
+    const int g0 = tr * NT + tid, gs = G * NT;
+    for (int i = g0; i < m; i += gs) {
+        d.perm[i] = i;
+        if (W > 0)
+            d.side[i] = d.A[(int64_t)i * d.stride];
+    }
+    for (int w = g0; w < W + 1; w += gs)
+        d.pmask[w] = 0;
+    if (tr == 0 && tid < 2) {
+        PanelState &q = d.st[tid];
+        q.nwin = q.nx = q.r_cur = q.r_next = q.kbar = q.status = q.zero_tail = q.nz = q.mode = 0;
+        q.r_switch = 0;
+        q.J = 0;
+        q.pop = 0;
+    }
+    if (!team_barrier(bar, target, G, pl))
+        return false;
+    for (int b = 0; b < W; ++b) {
+        if (tr == 0 && tid < PIVOT_THREADS)
+            pivot_panel(d.A, d.stride, d.side + (size_t)((b + 1) & 1) * m, d.perm, d.st + ((b + 1) & 1),
+                        d.st + (b & 1), d.P, d.Q, m, b, min(64, d.n - 64 * b), 0, 0);
+        if (!team_barrier(bar, target, G, pl))
+            return false;
+        sweep_panel16<0>(S, d.A, d.stride, d.side + (size_t)(b & 1) * m, d.side + (size_t)((b + 1) & 1) * m, d.perm,
+                         d.st + (b & 1), d.out, d.ostride, nullptr, m, W, b, tr, G);
+        if (!team_barrier(bar, target, G, pl))
+            return false;
+    }
+    const PanelState *stf = gf2::final_state(d.st, W);
+    if (tr == 0)
+        apply_order(d.perm, stf);
+    if (!team_barrier(bar, target, G, pl))
+        return false;
+    gather_rows(d.A, d.stride, d.perm, stf, d.P, d.Q, d.out, d.ostride, m, d.n, W, d.rank, tr, G);
+    if (!team_barrier(bar, target, G, pl))
+        return false;
+    pivot_mask(d.Q, stf, d.pmask, tr, G);
+    if (!team_barrier(bar, target, G, pl))
+        return false;
+    for (int i = g0; i < m; i += gs)
+        compress_row(d.out, d.ostride, d.Q, d.pmask, stf, m, i);
+    if (!team_barrier(bar, target, G, pl))
+        return false;
+    const int lane = tid & 31;
+    for (int i = (tr * NT + tid) >> 5; i < m; i += gs >> 5) {
+        const uint64_t *src = d.out + (int64_t)i * d.ostride;
+        uint64_t *dst = d.A + (int64_t)i * d.stride;
+        for (int w = lane; w < W; w += 32)
+            dst[w] = src[w];
+    }
+    return team_barrier(bar, target, G, pl);
+}
+
+__global__ void __launch_bounds__(NT, 1) k_batch_persist(const gf2::ElimDesc *__restrict__ D, PersistPlan pl)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    SweepSmem &S = *reinterpret_cast<SweepSmem *>(smraw);
+    __shared__ int s_item;
+    const int cta = blockIdx.x;
+    const int t = pl.team_of[cta];
+    if (t >= 0) {
+        const int G = pl.team_size[t], tr = cta - pl.team_start[t];
+        unsigned target = 0;
+        for (int k = pl.team_first[t]; k < pl.team_first[t + 1]; ++k)
+            if (!team_eliminate(S, D[pl.big[k]], tr, G, pl.bars + t, target, pl))
+                return;
+    }
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_item = *(volatile int *)pl.abort ? pl.nsmall : atomicAdd(pl.next_small, 1);
+        __syncthreads();
+        const int k = s_item;
+        __syncthreads();
+        if (k >= pl.nsmall)
+            return;
+        unsigned target = 0;
+        team_eliminate(S, D[pl.small[k]], 0, 1, nullptr, target, pl);
+    }
+}
+
 }  // namespace
 
 namespace gf2 {
@@ -1474,6 +1628,65 @@ int batch_finish(const ElimDesc *D, int count, int max_m, cudaStream_t s)
     k_copyback_b<<<dim3(gx < 16 ? gx : 16, (unsigned)count), 256, 0, s>>>(D);
     prof_launched(5);
     return note_cuda(cudaGetLastError());
+}
+
+// One persistent, cooperative launch of the whole batch (k_batch_persist). The plan arrays are
+// device memory: team_first (nteams + 1), big, small; the counters (next_small, bars[nteams],
+// abort) are zeroed here before the launch.
+int batch_persistent(const ElimDesc *D, int nteams, const PersistArrays &a, int nsmall, int *counters,
+                     cudaStream_t s)
+{
+    static std::atomic<unsigned long long> attr_devs{0};
+    const size_t smem = sizeof(SweepSmem);
+    if (attr_needed(attr_devs)) {
+        cudaError_t err = cudaFuncSetAttribute(k_batch_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess)
+            return note_cuda(err);
+        attr_done(attr_devs);
+    }
+    cudaError_t err = cudaMemsetAsync(counters, 0, (size_t)(nteams + 2) * sizeof(int), s);
+    if (err != cudaSuccess)
+        return note_cuda(err);
+    PersistPlan pl{};
+    pl.nteams = nteams;
+    pl.team_of = a.team_of;
+    pl.team_start = a.team_start;
+    pl.team_size = a.team_size;
+    pl.team_first = a.team_first;
+    pl.big = a.big;
+    pl.small = a.small;
+    pl.nsmall = nsmall;
+    pl.next_small = counters;
+    pl.abort = counters + 1;
+    pl.bars = reinterpret_cast<unsigned *>(counters + 2);
+    pl.status = status_word();
+    int dev = 0, nsm = 0, per_sm = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess ||
+        (err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_persist, NT, smem)) != cudaSuccess)
+        return note_cuda(err);
+    if (per_sm < 1)
+        return GF2_ENOMEM;  // the kernel does not fit on an SM
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nsm);  // one CTA per SM, all resident
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int tok = prof_begin(s);
+    err = cudaLaunchKernelEx(&cfg, k_batch_persist, D, pl);
+    prof_end(s, GF2_PROF_SWEEP, tok);
+    prof_launched(1);
+    return note_cuda(err);
+}
+
+int batch_persistent_grid()
+{
+    return sm_count();
 }
 
 int identity_perm(int *perm, int64_t m, cudaStream_t s)

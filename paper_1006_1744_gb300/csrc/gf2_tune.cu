@@ -1,8 +1,8 @@
 // gf2_tune.cu -- autotuner for the performance knobs of gf2_opts.
 //
 // None of these knobs changes a result (the sweep's tile width, the recursive
-// split's cutoff, the XOR-table or tensor-core product); they only change the
-// time. gf2_autotune times the candidates on a synthetic matrix of the
+// split's cutoff, the XOR-table or tensor-core product, the route to the
+// reduced echelon form); they only change the time. gf2_autotune times the candidates on a synthetic matrix of the
 // requested size and density on the current device and returns the fastest,
 // caching the answer per size and density bucket.
 #include <cmath>
@@ -102,6 +102,20 @@ extern "C" int gf2_autotune(int op, int64_t m, int64_t n, double density, gf2_op
     } else {
         for (int tw : {4, 8, 16})
             cands.push_back(opt(tw, 0, 0));
+        if (op == GF2_OP_RREF) {
+            // the direct reduced form (M4RI, Sec. 3.1) and the hybrid at the paper's two thresholds
+            for (int meth : {GF2_RREF_M4RI, GF2_RREF_HYBRID}) {
+                gf2_opts o = opt(16, 0, 0);
+                o.rref_method = meth;
+                if (meth == GF2_RREF_HYBRID)
+                    for (int pm : {150, 200}) {
+                        o.hybrid_permille = pm;
+                        cands.push_back(o);
+                    }
+                else
+                    cands.push_back(o);
+            }
+        }
         if (op == GF2_OP_PLS && n > 2 * 4096) {
             cands.push_back(opt(16, 4096, GF2_PRODUCT_XOR));
             cands.push_back(opt(16, 4096, GF2_PRODUCT_TENSOR));

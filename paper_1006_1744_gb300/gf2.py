@@ -23,6 +23,7 @@ _lib = None
 OP_PLS, OP_RREF, OP_RANK, OP_MUL = 1, 2, 3, 4
 PRODUCT_AUTO, PRODUCT_XOR, PRODUCT_TENSOR, PRODUCT_STRASSEN, PRODUCT_STRASSEN_TENSOR = 0, 1, 2, 3, 4
 RREF_AUTO, RREF_PLS, RREF_M4RI, RREF_HYBRID = 0, 1, 2, 3
+BATCH_AUTO, BATCH_STEPS, BATCH_PERSISTENT = 0, 1, 2
 
 _i64 = ctypes.c_int64
 _vp = ctypes.c_void_p
@@ -41,7 +42,8 @@ class Gf2Error(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("k", _int), ("tile_words", _int), ("grid_ctas", _int), ("product", _int),
-                ("cutoff_cols", _i64), ("rref_method", _int), ("hybrid_permille", _int), ("reserved", _int * 6)]
+                ("cutoff_cols", _i64), ("rref_method", _int), ("hybrid_permille", _int), ("batch_mode", _int),
+                ("reserved", _int * 5)]
 
 
 class BatchItem(ctypes.Structure):
@@ -298,4 +300,5 @@ def autotune(op: int, m: int, n: int, density: float = 0.5, stream=None):
     ms = ctypes.c_double(0.0)
     _check(lib().gf2_autotune(op, m, n, float(density), ctypes.byref(best), ctypes.byref(ms), _stream(stream)),
            "gf2_autotune")
-    return {"tile_words": best.tile_words, "cutoff_cols": best.cutoff_cols, "product": best.product}, ms.value
+    return {"tile_words": best.tile_words, "cutoff_cols": best.cutoff_cols, "product": best.product,
+            "rref_method": best.rref_method, "hybrid_permille": best.hybrid_permille}, ms.value

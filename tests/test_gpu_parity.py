@@ -261,8 +261,9 @@ def test_mul_parity(g, acc):
 @pytest.mark.parametrize("acc", [False, True])
 def test_mul_strassen_parity(g, product, acc):
     """Strassen-Winograd products (XOR-table and tensor-core leaves) equal the
-    plain product bit for bit: leaf size 512 gives up to three levels here, and
-    shapes that do not split fall back to the leaf form."""
+    plain product bit for bit: leaf size 512 gives up to two levels here (a
+    level needs k and n multiples of 2048), and shapes that do not split fall
+    back to the leaf form."""
     rng = np.random.default_rng(11 + product + 2 * acc)
     opts = {"product": product, "cutoff_cols": 512}
     for (m, k, n) in [(2048, 2048, 2048), (4096, 2048, 4096), (2048, 4096, 2048), (4096, 4096, 4096),
@@ -278,6 +279,46 @@ def test_mul_strassen_parity(g, product, acc):
         torch.cuda.synchronize()
         W = S.words_per_row(n)
         assert (host(Cd)[:, :W] == want[:, :W]).all(), (m, k, n)
+
+
+def test_mul_strassen_three_levels_and_wide_strides(g):
+    """Three Strassen-Winograd levels (8192 -> 4096 -> 2048 -> 1024-bit leaves, leaf
+    size 512), and every block view formed from row pitches wider than the
+    minimum (A, B and C each 16, 32 and 48 words wider): both leaf forms, with and
+    without accumulation, equal the oracle's product; C's padding words stay."""
+    m = k = n = 8192
+    A = S.dense(m, k, 71)
+    B = S.dense(k, n, 72)
+    C0 = S.dense(m, n, 73)
+    want = {False: oracle.mul(A, B, m, k, n, stride=C0.shape[1]), True: oracle.mul(A, B, m, k, n, C=C0)}
+    for product in (3, 4):
+        for acc in (False, True):
+            opts = {"product": product, "cutoff_cols": 512}
+            Cd = dev(C0)
+            g.mul(Cd, dev(A), dev(B), m, k, n, accumulate=acc, opts=opts)
+            torch.cuda.synchronize()
+            assert (host(Cd) == want[acc]).all(), (product, acc)
+    m = k = n = 4096
+    W = S.words_per_row(n)
+    A = S.dense(m, k, 81)
+    B = S.dense(k, n, 82)
+    C0 = S.dense(m, n, 83)
+
+    def wide(M, extra):
+        out = np.full((M.shape[0], M.shape[1] + extra), np.uint64(0x5A5A5A5A5A5A5A5A), dtype=np.uint64)
+        out[:, :W] = M[:, :W]
+        return out
+
+    want = {False: oracle.mul(A, B, m, k, n), True: oracle.mul(A, B, m, k, n, C=C0)}
+    for product in (3, 4):
+        for acc in (False, True):
+            Cd = dev(wide(C0, 48))
+            g.mul(Cd, dev(wide(A, 16)), dev(wide(B, 32)), m, k, n, accumulate=acc,
+                  opts={"product": product, "cutoff_cols": 512})
+            torch.cuda.synchronize()
+            got = host(Cd)
+            assert (got[:, :W] == want[acc][:, :W]).all(), ("wide", product, acc)
+            assert (got[:, W:] == np.uint64(0x5A5A5A5A5A5A5A5A)).all()
 
 
 def test_mul_strassen_internal_workspace_and_too_small(g):
@@ -439,7 +480,7 @@ def test_pls_batched_parity(g):
         hosts.append((A, m, n))
         mats.append(dev(A))
         ns.append(n)
-    for opts in (None, {"tile_words": 4}):
+    for opts in (None, {"tile_words": 4}, {"batch_mode": g.BATCH_STEPS}, {"batch_mode": g.BATCH_PERSISTENT}):
         ds = [t.clone() for t in mats]
         Ps, Qs, ranks = g.pls_batched(ds, ns, opts=opts)
         torch.cuda.synchronize()
@@ -454,9 +495,11 @@ def test_pls_batched_parity(g):
                 assert (host(ds[i])[:, :W] == R[:, :W]).all(), (i, m, n)
 
 
-def test_pls_batched_many_small_and_user_workspace(g):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_pls_batched_many_small_and_user_workspace(g, mode):
     """A batch of 300 small matrices of varied shape through a caller-owned
-    workspace, run twice (the workspace's previous contents do not matter)."""
+    workspace, run twice (the workspace's previous contents do not matter), with
+    both schedules (launches per panel step; one persistent launch)."""
     rng = np.random.default_rng(8)
     hosts, ns = [], []
     for i in range(300):
@@ -471,7 +514,7 @@ def test_pls_batched_many_small_and_user_workspace(g):
     want = [oracle.pls(A, m, n) for (A, m, n) in hosts]
     for _ in range(2):
         ds = [dev(A) for (A, _, _) in hosts]
-        Ps, Qs, ranks = g.pls_batched(ds, ns, work=work)
+        Ps, Qs, ranks = g.pls_batched(ds, ns, work=work, opts={"batch_mode": mode})
         torch.cuda.synchronize()
         rk = ranks.cpu().numpy()
         for i, (A, m, n) in enumerate(hosts):
@@ -482,7 +525,8 @@ def test_pls_batched_many_small_and_user_workspace(g):
             assert (host(ds[i])[:, :S.words_per_row(n)] == R[:, :S.words_per_row(n)]).all()
 
 
-def test_pls_batched_replayed_with_new_contents(g):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_pls_batched_replayed_with_new_contents(g, mode):
     """The same batch (buffers, ranks, workspace) called again is replayed from a
     captured graph, plan upload included; each call sees the current contents."""
     g.replay_enable(True)
@@ -501,7 +545,7 @@ def test_pls_batched_replayed_with_new_contents(g):
         hosts = [make(kinds[(i + it) % 4], m, n, 100 * it + i) for i, (m, n) in enumerate(shapes)]
         for D, A in zip(mats, hosts):
             D.copy_(torch.from_numpy(np.ascontiguousarray(A).view(np.int64)))
-        g.pls_batched(mats, ns, Ps=Ps, Qs=Qs, ranks=ranks, work=work)
+        g.pls_batched(mats, ns, Ps=Ps, Qs=Qs, ranks=ranks, work=work, opts={"batch_mode": mode})
         torch.cuda.synchronize()
         rk = ranks.cpu().numpy()
         for i, ((m, n), A) in enumerate(zip(shapes, hosts)):
@@ -512,6 +556,30 @@ def test_pls_batched_replayed_with_new_contents(g):
             assert (host(mats[i])[:, :W] == R[:, :W]).all(), (it, i)
     c1, r1 = g.replay_stats()
     assert c1 - c0 == 1 and r1 - r0 == 3, (c1 - c0, r1 - r0)
+
+
+def test_pls_batched_persistent_teams(g):
+    """A batch whose large members go to teams of several CTAs in the persistent
+    launch (team barriers between pivot search and sweep), mixed with small ones:
+    every member equals the oracle, as with the per-step schedule."""
+    rng = np.random.default_rng(44)
+    shapes = [(3000, 4000), (2500, 2500), (4096, 2048), (2000, 3000)] + \
+             [(int(rng.integers(1, 300)), int(rng.integers(1, 400))) for _ in range(60)]
+    kinds = ["dense", "sparse01", "lowrank", "echelon", "deep"]
+    hosts = [(make(kinds[i % 5], m, n, 900 + i), m, n) for i, (m, n) in enumerate(shapes)]
+    want = [oracle.pls(A, m, n) for (A, m, n) in hosts]
+    for mode in (g.BATCH_PERSISTENT, g.BATCH_STEPS):
+        ds = [dev(A) for (A, _, _) in hosts]
+        Ps, Qs, ranks = g.pls_batched(ds, [n for (_, _, n) in hosts], opts={"batch_mode": mode})
+        torch.cuda.synchronize()
+        assert g.sync_status() == 0
+        rk = ranks.cpu().numpy()
+        for i, (A, m, n) in enumerate(hosts):
+            R, P, Q, r = want[i]
+            assert rk[i] == r, (mode, i)
+            assert (Ps[i].cpu().numpy()[:m] == P[:m]).all() and (Qs[i].cpu().numpy()[:n] == Q[:n]).all(), (mode, i)
+            W = S.words_per_row(n)
+            assert (host(ds[i])[:, :W] == R[:, :W]).all(), (mode, i)
 
 
 def test_autotune_choices_are_exact_and_cached(g):
@@ -533,4 +601,16 @@ def test_autotune_choices_are_exact_and_cached(g):
     g.mul(C, dev(A), dev(B), 300, 1024, 700, opts=om)
     torch.cuda.synchronize()
     assert (host(C)[:, :11] == want[:, :11]).all()
+    # RREF: the route (PLS, M4RI, hybrid) is among the candidates; the choice is exact
+    for (mr, nr, dens) in [(1200, 1700, 0.5), (1500, 1500, 0.02)]:
+        orr, _ = g.autotune(g.OP_RREF, mr, nr, dens)
+        assert orr["rref_method"] in (0, 2, 3)
+        A = S.bernoulli(mr, nr, dens, 123) if dens < 0.5 else S.dense(mr, nr, 123)
+        R, piv, r = oracle.rref(A, mr, nr)
+        D = dev(A)
+        rd, pd = g.rref(D, nr, opts=orr)
+        torch.cuda.synchronize()
+        W = S.words_per_row(nr)
+        assert int(rd.item()) == r and (pd.cpu().numpy()[:r] == piv).all()
+        assert (host(D)[:, :W] == R[:, :W]).all()
     assert g.sync_status() == 0
