@@ -327,12 +327,23 @@ def run_config3(args):
                 gbs = byts / (ms * 1e-3) / 1e9
                 results[variant][name].update({"sweep_algorithmic_GB": byts / 1e9, "sweep_GBps_over_elimination": gbs,
                                                "hbm_frac": gbs / hbm})
+        # the same matrix to its reduced echelon form by each route of gf2_rref
+        wr = gf2.new_workspace(gf2.OP_RREF, n, n, device=dev)
+        rk = torch.empty(1, dtype=torch.int64, device=dev)
+        piv = torch.empty(n, dtype=torch.int64, device=dev)
+        for name, meth in (("rref_pls_route", gf2.RREF_PLS), ("rref_m4ri", gf2.RREF_M4RI),
+                           ("rref_hybrid", gf2.RREF_HYBRID)):
+            ms = _timed(lambda: gf2.rref(A, n, rank=rk, pivots=piv, work=wr, opts={"rref_method": meth}), steps, 1,
+                        pre=lambda: A.copy_(A0))
+            results[variant][name] = {"ms": ms, "rank": int(rk.item())}
+        del wr
         torch.cuda.empty_cache()
     gf2.prof_enable(0)
     clocks = sampler.stop()
     best = results["dense"]["mmpf"]["ms"]
     speed = {v: {"rec_tc_over_rec_xor": r["rec_xor"]["ms"] / r["rec_tc"]["ms"],
-                 "mmpf_over_rec_xor": r["rec_xor"]["ms"] / r["mmpf"]["ms"]} for v, r in results.items()}
+                 "mmpf_over_rec_xor": r["rec_xor"]["ms"] / r["mmpf"]["ms"],
+                 "mmpf_over_rec_tc": r["rec_tc"]["ms"] / r["mmpf"]["ms"]} for v, r in results.items()}
     _base_line(args, best / 1e3, "s", best,
                {"workload": "65536x65536 GF(2): dense Bernoulli(1/2), A=B.C (B 65536x32768, C 32768x65536), "
                             "Bernoulli(0.01); gf2_pls by MMPF panels and by the recursive PLS (cutoff 4096 columns) "

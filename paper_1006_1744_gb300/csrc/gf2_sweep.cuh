@@ -19,6 +19,7 @@ struct SweepSmem {
     u64 Z[256 * 16];      // panel byte v at byte position q -> coordinates over O, two copies: v * 16 + copy * 8 + q
     u64 O[64 * TW];       // rows of the tables for the current tile
     u64 map[64];          // zmap of the panel
+    int prow[64];         // physical rows of the pivots
 };
 
 // row codes: >= 0 trailing row (physical index), -1 none, -2 row above (MODE 1, kept in
@@ -326,16 +327,28 @@ __device__ __forceinline__ void sweep_body(Cfg &c, SweepSmem &S, unsigned long l
     const int plain_from = c.nx ? INT_MAX : c.r + max(c.kbar, c.nwin);
     const int plain_blk = c.nx ? nblk : min(nblk, (plain_from - c.row0 + RPU - 1) / RPU);
 
-    if (tid < 64)
+    if (tid < 64) {
         S.map[tid] = st->zmap[tid];
+        S.prow[tid] = tid < c.kbar ? st->prow[tid] : 0;
+    }
     __syncthreads();
-    for (int e = tid; e < 256 * 16; e += NT) {
-        const int v = e >> 4, q = e & 7;
-        u64 zz = 0;
+    if (tid < 8 * 16) {
+        // coordinate table of byte position q, entries (vh << 4) | low in Gray-code order of the
+        // low nibble (one XOR per entry), both copies
+        const int q = tid >> 4, vh = tid & 15;
+        const u64 *mq = S.map + 8 * q;
+        u64 cur = 0;
 #pragma unroll
-        for (int bit = 0; bit < 8; ++bit)
-            zz ^= ((v >> bit) & 1) ? S.map[8 * q + bit] : 0ull;
-        S.Z[e] = zz;
+        for (int bit = 0; bit < 4; ++bit)
+            cur ^= ((vh >> bit) & 1) ? mq[4 + bit] : 0ull;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if (i)
+                cur ^= mq[__ffs(i) - 1];
+            const int v = (vh << 4) | (i ^ (i >> 1));
+            S.Z[v * 16 + q] = cur;
+            S.Z[v * 16 + 8 + q] = cur;
+        }
     }
     Lanes L;
     L.sub = tid & (TPR - 1);
@@ -357,7 +370,7 @@ __device__ __forceinline__ void sweep_body(Cfg &c, SweepSmem &S, unsigned long l
             const int t = e / TW, w = wbase + e % TW;
             u64 v = 0;
             if (t < c.kbar && w < W && w >= b) {
-                const int pr = st->prow[t];
+                const int pr = S.prow[t];
                 if (w > b)
                     v = A[(int64_t)pr * stride + w];
                 else if (MODE)
