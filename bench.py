@@ -443,9 +443,13 @@ def run_config4(args):
 def run_config5(args):
     """Request stream: echelon-structured matrices arriving as a Poisson process at
     0.5, 0.8 and 1.0 times the measured capacity. Matrices are generated and kept on
-    the device; whenever the GPU is free, every request that has arrived is admitted
-    as long as the batch's workspace fits the budget set from free device memory,
-    and the batch runs as one gf2_pls_batched call. Latency = completion - arrival."""
+    the device. The server has two lanes, each with its own stream and workspace: small
+    requests (m < 8192) and large ones. Whenever a lane is idle, every request of its
+    class that has arrived is admitted as long as the lane's workspace budget allows, and
+    runs as one gf2_pls_batched call on the lane's stream (the per-step schedule, whose
+    launches from the two lanes run side by side); a lane's batch completes when its event
+    does. Latency = completion - arrival. Capacity = the same server with every request
+    queued at time 0."""
     import numpy as np
     import torch
     from paper_1006_1744_gb300 import build, gf2, synth, synth_gpu
@@ -466,40 +470,79 @@ def run_config5(args):
     shapes = [(m, n, synth.default_stride(n)) for (m, n, sd) in rec]
     ws_each = [gf2.pls_batched_workspace_bytes([sh]) for sh in shapes]
     free, _total = torch.cuda.mem_get_info(dev)
-    budget = int(min(free * 0.6, gf2.pls_batched_workspace_bytes(shapes)))
-    work = torch.empty(budget // 8 + 64, dtype=torch.int64, device=dev)
+    total_budget = int(free * 0.6)
+    SPLIT = 8192
+    classes = [[i for i in range(R) if rec[i][0] < SPLIT], [i for i in range(R) if rec[i][0] >= SPLIT]]
+    shares = (0.25, 0.75)
+    lanes = []
+    for c, share in zip(classes, shares):
+        need = gf2.pls_batched_workspace_bytes([shapes[i] for i in c]) if c else 0
+        bud = int(min(total_budget * share, need)) if c else 0
+        bud = max(bud, max((ws_each[i] for i in c), default=0))
+        lanes.append({"ids": c, "budget": bud, "stream": torch.cuda.Stream(device=dev),
+                      "work": torch.empty(max(bud, 256) // 8 + 64, dtype=torch.int64, device=dev)})
+    opts = {"batch_mode": gf2.BATCH_STEPS}
 
-    def run_batch(ids):
-        for i in ids:
-            mats[i].copy_(mats0[i])
-        Pi = [Ps[i] for i in ids]
-        Qi = [Qs[i] for i in ids]
-        rk = torch.empty(len(ids), dtype=torch.int64, device=dev)
-        gf2.pls_batched([mats[i] for i in ids], [ns[i] for i in ids], Pi, Qi, rk, work=work)
-        return rk
+    def launch(lane, ids):
+        with torch.cuda.stream(lane["stream"]):
+            for i in ids:
+                mats[i].copy_(mats0[i])
+            rk = torch.empty(len(ids), dtype=torch.int64, device=dev)
+            gf2.pls_batched([mats[i] for i in ids], [ns[i] for i in ids], [Ps[i] for i in ids],
+                            [Qs[i] for i in ids], rk, work=lane["work"], opts=opts, stream=lane["stream"])
+            ev = torch.cuda.Event()
+            ev.record(lane["stream"])
+        return rk, ev
 
-    def take(order, start):
-        """Indices from order[start:] while the batch workspace fits the budget."""
-        ids, need = [], 0
-        for i in order[start:]:
-            if ids and need + ws_each[i] > budget:
-                break
-            ids.append(i)
-            need += ws_each[i]
-        return ids
+    def serve(arr):
+        """Run the whole stream with arrival times arr (seconds); returns completion times, batches."""
+        comp = np.zeros(R)
+        nb = 0
+        state = [{"next": 0, "inflight": None} for _ in lanes]
+        start = time.perf_counter()
+        remaining = R
+        while remaining:
+            now = time.perf_counter() - start
+            busy = False
+            for L, st in zip(lanes, state):
+                if st["inflight"] is not None:
+                    ids, rk, ev = st["inflight"]
+                    if not ev.query():
+                        busy = True
+                        continue
+                    t = time.perf_counter() - start
+                    comp[ids] = t
+                    ranks[ids] = rk
+                    remaining -= len(ids)
+                    st["inflight"] = None
+                c = L["ids"]
+                ids, need = [], 0
+                k = st["next"]
+                while k < len(c) and arr[c[k]] <= now:
+                    if ids and need + ws_each[c[k]] > L["budget"]:
+                        break
+                    ids.append(c[k])
+                    need += ws_each[c[k]]
+                    k += 1
+                if ids:
+                    st["next"] = k
+                    rk, ev = launch(L, ids)
+                    st["inflight"] = (ids, rk, ev)
+                    nb += 1
+                    busy = True
+            if not busy:
+                pending = [arr[L["ids"][st["next"]]] for L, st in zip(lanes, state) if st["next"] < len(L["ids"])]
+                if pending:
+                    time.sleep(max(0.0, min(min(pending) - (time.perf_counter() - start), 0.0005)))
+            else:
+                time.sleep(0.0001)
+        return comp, nb
 
-    # capacity: requests per second when everything is queued at once
-    run_batch(take(list(range(R)), 0))
+    serve(np.zeros(R))  # warm-up (first calls, graph captures)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    done = 0
-    while done < R:
-        ids = take(list(range(R)), done)
-        rk = run_batch(ids)
-        torch.cuda.synchronize()
-        ranks[done:done + len(ids)] = rk
-        done += len(ids)
-    capacity = R / (time.perf_counter() - t0)
+    comp0, _ = serve(np.zeros(R))
+    capacity = R / comp0.max()
 
     sampler = ClockSampler(0)
     sampler.start()
@@ -509,25 +552,14 @@ def run_config5(args):
     for frac in (0.5, 0.8, 1.0):
         lam = frac * capacity
         arr = synth.arrival_times(R, lam, SEED + int(frac * 100))
-        comp = np.zeros(R)
-        nbatch, nxt = 0, 0
-        start = time.perf_counter()
-        while nxt < R:
-            now = time.perf_counter() - start
-            if arr[nxt] > now:
-                time.sleep(min(arr[nxt] - now, 0.0005))
-                continue
-            arrived = int(np.searchsorted(arr, now, side="right"))
-            ids = take(list(range(arrived)), nxt)
-            run_batch(ids)
-            torch.cuda.synchronize()
-            comp[ids] = time.perf_counter() - start
-            nxt += len(ids)
-            nbatch += 1
+        comp, nbatch = serve(arr)
         lat = comp - arr
+        small = np.array([rec[i][0] < SPLIT for i in range(R)])
         results[f"{frac:.1f}"] = {
-            "rate_per_s": lam, "throughput_per_s": R / comp[-1], "p50_ms": float(np.percentile(lat, 50) * 1e3),
-            "p99_ms": float(np.percentile(lat, 99) * 1e3), "batches": nbatch, "mean_batch": R / nbatch}
+            "rate_per_s": lam, "throughput_per_s": R / comp.max(), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "batches": nbatch, "mean_batch": R / nbatch,
+            "p99_small_ms": float(np.percentile(lat[small], 99) * 1e3) if small.any() else None,
+            "p99_large_ms": float(np.percentile(lat[~small], 99) * 1e3) if (~small).any() else None}
     launches = gf2.prof_launches()
     gf2.prof_enable(0)
     clocks = sampler.stop()
@@ -535,11 +567,13 @@ def run_config5(args):
     _base_line(args, v / 1e3, "s", v,
                {"workload": "request stream: echelon-structured GF(2) matrices (m log-uniform in [512, 32768], "
                             "n = m to 2m, row i zero before column 0.5 i n / m, Bernoulli(0.3) after), Poisson "
-                            "arrivals at 0.5, 0.8, 1.0 x capacity, batched as they arrive, PLS + rank",
+                            "arrivals at 0.5, 0.8, 1.0 x capacity, batched as they arrive in two lanes (m < 8192, "
+                            "m >= 8192), PLS + rank",
                 "requests": R, "seed": SEED, "value_is": "p99 latency at 0.8 x capacity",
-                "workspace_budget_bytes": budget},
+                "workspace_budget_bytes": [L["budget"] for L in lanes]},
                clocks, launches,
-               {"capacity_per_s": capacity, "by_load": results, "rank_sum": int(ranks.sum().item())})
+               {"capacity_per_s": capacity, "by_load": results, "rank_sum": int(ranks.sum().item()),
+                "requests_by_lane": [len(c) for c in classes]})
     return 0
 
 

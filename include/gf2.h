@@ -80,7 +80,10 @@ extern "C" {
  * defaults; a field left 0 means "choose automatically".
  */
 typedef struct gf2_opts {
-    int k;              /* bits per Gray-code table (Sec. 3.1); only 8 is built, 0 = 8 */
+    int k;              /* bits per Gray-code table (Sec. 3.1): 8 (0 = 8; stored as 7-bit halves plus one
+                           table of the groups' top bits) or 4 (16 tables of 16 entries: cheaper to build,
+                           more lookups; the 16-word PLS-form sweeps only: not with the reduced-form RREF
+                           routes, tile_words 4 or 8, or the persistent batch) */
     int tile_words;     /* column tile of a table sweep, in words: 0 (default), 4, 8 or 16 */
     int grid_ctas;      /* CTAs of a table sweep; 0 = one per SM but one (left to the overlapping pivot search) */
     int product;        /* GF2_PRODUCT_*; used by gf2_mul */
@@ -225,6 +228,22 @@ typedef struct {
 size_t gf2_pls_batched_workspace_bytes(const gf2_batch_item *items, int64_t count, const gf2_opts *opts);
 int gf2_pls_batched(const gf2_batch_item *items, int64_t count, int64_t *ranks, void *work, size_t work_bytes,
                     const gf2_opts *opts, void *stream);
+
+/*
+ * The persistent schedule's plan, on the host only (no device call): which
+ * matrices of a gf2_pls_batched call get a team of CTAs and which go to the
+ * device work queue, for a launch of `ctas` CTAs (gf2_pls_batched uses one
+ * per SM). The plan reads only m and n of the items. Outputs are host arrays:
+ *   team_of     -- int[ctas]: the team of each CTA, or -1 (a queue worker);
+ *                  every team is a contiguous range of a power-of-two number
+ *                  of CTAs;
+ *   team_size   -- int[ctas] (at most ctas / 2 teams are written): CTAs per team;
+ *   member_team -- int[count]: the team of each matrix, or -1 for the queue.
+ * Returns the number of teams, or -1 for invalid arguments (bad sizes, ctas
+ * outside [1, 1024], a NULL output).
+ */
+int gf2_batch_plan(const gf2_batch_item *items, int64_t count, int ctas, int *team_of, int *team_size,
+                   int *member_team);
 
 /*
  * Rank without allocating device memory. The paper has no counterpart. Some

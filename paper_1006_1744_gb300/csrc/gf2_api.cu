@@ -146,8 +146,11 @@ int check_opts(const gf2_opts *o)
 {
     if (!o)
         return GF2_OK;
-    if (o->k != 0 && o->k != 8)
+    if (o->k != 0 && o->k != 4 && o->k != 8)
         return GF2_EINVAL;
+    if (o->k == 4 && ((o->tile_words != 0 && o->tile_words != 16) || o->rref_method == GF2_RREF_M4RI ||
+                      o->rref_method == GF2_RREF_HYBRID || o->batch_mode == GF2_BATCH_PERSISTENT))
+        return GF2_EINVAL;  // k = 4 is built into the 16-word PLS-form sweep only
     if (o->tile_words != 0 && o->tile_words != 4 && o->tile_words != 8 && o->tile_words != 16)
         return GF2_EINVAL;
     if (o->grid_ctas < 0 || o->product < 0 || o->product > GF2_PRODUCT_STRASSEN_TENSOR || o->cutoff_cols < 0)
@@ -187,6 +190,7 @@ static Elim make_elim(uint64_t *A, int64_t m, int64_t n, int64_t stride, char *w
     e.tile_words = (o && o->tile_words) ? o->tile_words : 16;
     e.mode = 0;
     e.hybrid_permille = o ? o->hybrid_permille : 0;
+    e.k = (o && o->k) ? o->k : 8;
     // default: one CTA per SM but one, so the look-ahead pivot search (which cannot share an
     // SM with a 1024-thread sweep CTA) never holds back a CTA of the sweep it overlaps
     const int nsm = sm_count();
@@ -236,7 +240,7 @@ static CallKey call_key(int op, const void *A, int64_t m, int64_t n, int64_t str
     cudaGetDevice(&k.device);
     k.op = op;
     k.tile_words = e.tile_words;
-    k.grid = e.grid;
+    k.grid = e.grid + (e.k << 27);  // the table width changes the launches too
     k.A = A;
     k.m = m;
     k.n = n;

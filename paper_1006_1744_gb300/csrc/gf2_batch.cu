@@ -134,7 +134,7 @@ int check_items(const gf2_batch_item *items, int64_t count)
 }
 
 int batched_run(const gf2_batch_item *items, int64_t count, int64_t *ranks, char *w, const BatchLayout &L, int tw,
-                int mode, cudaStream_t s);
+                int mode, int kbits, cudaStream_t s);
 bool persistent_suits(const gf2_batch_item *items, int64_t count);
 
 }  // namespace
@@ -162,9 +162,10 @@ int gf2_pls_batched(const gf2_batch_item *items, int64_t count, int64_t *ranks, 
     if ((rc = gf2::get_work(work, work_bytes, L.total)))
         return rc;
     const int tw = (opts && opts->tile_words) ? opts->tile_words : 16;
+    const int kbits = (opts && opts->k) ? opts->k : 8;
     int mode = opts ? opts->batch_mode : GF2_BATCH_AUTO;
     if (mode == GF2_BATCH_AUTO)
-        mode = tw == 16 && persistent_suits(items, count) ? GF2_BATCH_PERSISTENT : GF2_BATCH_STEPS;
+        mode = tw == 16 && kbits == 8 && persistent_suits(items, count) ? GF2_BATCH_PERSISTENT : GF2_BATCH_STEPS;
     if (mode == GF2_BATCH_PERSISTENT && tw != 16)
         return GF2_EINVAL;  // the persistent schedule runs the 16-word sweep
     // a repeated call (same items, ranks, workspace, options) replays a captured graph
@@ -173,14 +174,14 @@ int gf2_pls_batched(const gf2_batch_item *items, int64_t count, int64_t *ranks, 
     cudaGetDevice(&key.device);
     key.op = -GF2_OP_PLS;
     key.tile_words = tw;
-    key.grid = mode;
+    key.grid = mode + (kbits << 8);
     key.m = count;
     key.rank = ranks;
     key.work = work;
     key.work_bytes = work_bytes;
     return gf2::run_replayed(
         key, (cudaStream_t)stream,
-        [&](cudaStream_t s) { return batched_run(items, count, ranks, (char *)work, L, tw, mode, s); }, items,
+        [&](cudaStream_t s) { return batched_run(items, count, ranks, (char *)work, L, tw, mode, kbits, s); }, items,
         (size_t)count * sizeof(gf2_batch_item), L.mats);
 }
 
@@ -300,7 +301,7 @@ bool persistent_suits(const gf2_batch_item *items, int64_t count)
 }
 
 int batched_run(const gf2_batch_item *items, int64_t count, int64_t *ranks, char *w, const BatchLayout &L, int tw,
-                int mode, cudaStream_t s)
+                int mode, int kbits, cudaStream_t s)
 {
     int rc = GF2_OK;
 
@@ -432,7 +433,7 @@ int batched_run(const gf2_batch_item *items, int64_t count, int64_t *ranks, char
         if ((rc = gf2::note_cuda(cudaEventRecord(ev_piv, s))) || (rc = gf2::note_cuda(cudaStreamWaitEvent(t, ev_piv, 0))))
             return rc;
         rc = sweep16 ? gf2::batch_sweep16(dD, dIdx + step_idx_off[b], dPre + step_pre_off[b], step_nact[b],
-                                          step_total[b], b, t)
+                                          step_total[b], b, kbits, t)
                      : gf2::batch_sweep(dD, dIdx + step_idx_off[b], dPre + step_pre_off[b], step_nact[b],
                                         step_total[b], b, tw, t);
         if (rc)
@@ -451,3 +452,34 @@ int batched_run(const gf2_batch_item *items, int64_t count, int64_t *ranks, char
 }
 
 }  // namespace
+
+/*
+ * Diagnostic (host only): the persistent schedule's plan for these shapes on `ctas` CTAs.
+ * team_of (length ctas): each CTA's team or -1; team_size (length >= teams); member_team
+ * (length count): each matrix's team, or -1 for the work queue. Returns the team count, or -1
+ * for invalid arguments.
+ */
+extern "C" int gf2_batch_plan(const gf2_batch_item *items, int64_t count, int ctas, int *team_of, int *team_size,
+                              int *member_team)
+{
+    if (check_sizes(items, count) || ctas <= 0 || ctas > MAX_CTAS || !team_of || !team_size || !member_team)
+        return -1;
+    std::vector<gf2::ElimDesc> D((size_t)count);
+    for (int64_t i = 0; i < count; ++i) {
+        D[i] = gf2::ElimDesc{};
+        D[i].m = (int)items[i].m;
+        D[i].n = (int)items[i].n;
+        D[i].W = (int)((items[i].n + 63) / 64);
+    }
+    const PersistHostPlan P = plan_persistent(D.data(), count, ctas);
+    for (int c = 0; c < ctas; ++c)
+        team_of[c] = P.team_of[c];
+    for (int t = 0; t < P.nteams; ++t)
+        team_size[t] = P.team_size[t];
+    for (int64_t i = 0; i < count; ++i)
+        member_team[i] = -1;
+    for (int t = 0; t < P.nteams; ++t)
+        for (int k = P.team_first[t]; k < P.team_first[t + 1]; ++k)
+            member_team[P.big[k]] = t;
+    return P.nteams;
+}

@@ -265,6 +265,7 @@ struct Elim {
     int mode;         // table sweeps: 0 = PLS (trailing rows), 1 = reduced echelon form (every row),
                       // 2 = hybrid (reduced form until the density reaches hybrid_permille, then PLS)
     int hybrid_permille;
+    int k;            // bits per Gray-code table of the 16-word PLS-form sweep: 8 or 4
 };
 
 // One matrix of a batched elimination (device-resident array, one per matrix).
@@ -303,7 +304,7 @@ int sweep_rows_per_pass(int tile_words);
 // table sweep of panel b over 16-word tiles (gf2_sweep.cu), in the form e.mode selects
 int launch_sweep16(const Elim &e, int b, cudaStream_t s);
 // the same for panel b of a batch (PLS form), CTAs shared out as for batch_sweep
-int batch_sweep16(const ElimDesc *D, const int *idx, const int *pre, int nact, int total, int b, cudaStream_t s);
+int batch_sweep16(const ElimDesc *D, const int *idx, const int *pre, int nact, int total, int b, int k, cudaStream_t s);
 constexpr int SWEEP16_ROWS = 128;  // rows per block of work of the 16-word sweep
 int sweep_ctas_per_sm(int tile_words);
 

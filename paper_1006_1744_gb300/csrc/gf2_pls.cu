@@ -1500,7 +1500,7 @@ __device__ bool team_eliminate(SweepSmem &S, const gf2::ElimDesc &d, int tr, int
                         d.st + (b & 1), d.P, d.Q, m, b, min(64, d.n - 64 * b), 0, 0);
         if (!team_barrier(bar, target, G, pl))
             return false;
-        sweep_panel16<0>(S, d.A, d.stride, d.side + (size_t)(b & 1) * m, d.side + (size_t)((b + 1) & 1) * m, d.perm,
+        sweep_panel16<0, 8>(S, d.A, d.stride, d.side + (size_t)(b & 1) * m, d.side + (size_t)((b + 1) & 1) * m, d.perm,
                          d.st + (b & 1), d.out, d.ostride, nullptr, m, W, b, tr, G);
         if (!team_barrier(bar, target, G, pl))
             return false;

@@ -39,18 +39,19 @@
 
 namespace {
 
-template <int FORM>
+template <int FORM, int KB>
 __global__ void __launch_bounds__(NT, 1)
 k_sweep16(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_cur, u64 *__restrict__ side_nxt,
           const int *__restrict__ perm, const PanelState *__restrict__ st, uint64_t *__restrict__ out,
           int64_t ostride, u64 *__restrict__ ups, int m, int W, int b)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    sweep_panel16<FORM>(*reinterpret_cast<SweepSmem *>(smraw), A, stride, side_cur, side_nxt, perm, st, out, ostride,
+    sweep_panel16<FORM, KB>(*reinterpret_cast<SweepSmem *>(smraw), A, stride, side_cur, side_nxt, perm, st, out, ostride,
                         ups, m, W, b, blockIdx.x, gridDim.x);
 }
 
 // Batched: panel b of the nact matrices idx[0..nact), matrix idx[j] swept by CTAs pre[j] .. pre[j+1]-1.
+template <int KB>
 __global__ void __launch_bounds__(NT, 1)
 k_sweep16_b(const gf2::ElimDesc *__restrict__ D, const int *__restrict__ idx, const int *__restrict__ pre, int nact,
             int b)
@@ -65,20 +66,20 @@ k_sweep16_b(const gf2::ElimDesc *__restrict__ D, const int *__restrict__ idx, co
             hi = mid - 1;
     }
     const gf2::ElimDesc &d = D[idx[lo]];
-    sweep_panel16<0>(*reinterpret_cast<SweepSmem *>(smraw), d.A, d.stride, d.side + (size_t)(b & 1) * d.m,
+    sweep_panel16<0, KB>(*reinterpret_cast<SweepSmem *>(smraw), d.A, d.stride, d.side + (size_t)(b & 1) * d.m,
                      d.side + (size_t)((b + 1) & 1) * d.m, d.perm, d.st + (b & 1), d.out, d.ostride, nullptr, d.m, d.W,
                      b, (int)blockIdx.x - pre[lo], pre[lo + 1] - pre[lo]);
 }
 
 constexpr size_t SWEEP_SMEM = sizeof(SweepSmem);
 
-template <int FORM>
+template <int FORM, int KB>
 int launch(const gf2::Elim &e, int b, cudaStream_t s)
 {
     static std::atomic<unsigned long long> attr_devs{0};
     if (gf2::attr_needed(attr_devs)) {
         cudaError_t err =
-            cudaFuncSetAttribute(k_sweep16<FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
+            cudaFuncSetAttribute(k_sweep16<FORM, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
         if (err != cudaSuccess)
             return gf2::note_cuda(err);
         gf2::attr_done(attr_devs);
@@ -86,7 +87,7 @@ int launch(const gf2::Elim &e, int b, cudaStream_t s)
     const u64 *cur = e.side + (size_t)(b & 1) * e.m;
     u64 *nxt = e.side + (size_t)((b + 1) & 1) * e.m;
     const int tok = gf2::prof_begin(s);
-    k_sweep16<FORM><<<e.grid, NT, SWEEP_SMEM, s>>>(e.A, e.stride, cur, nxt, e.perm, e.st + (b & 1), e.out, e.ostride,
+    k_sweep16<FORM, KB><<<e.grid, NT, SWEEP_SMEM, s>>>(e.A, e.stride, cur, nxt, e.perm, e.st + (b & 1), e.out, e.ostride,
                                                    e.ups, (int)e.m, (int)e.W, b);
     gf2::prof_end(s, GF2_PROF_SWEEP, tok);
     gf2::prof_launched(1);
@@ -97,29 +98,41 @@ int launch(const gf2::Elim &e, int b, cudaStream_t s)
 
 namespace gf2 {
 
-int batch_sweep16(const ElimDesc *D, const int *idx, const int *pre, int nact, int total, int b, cudaStream_t s)
+template <int KB>
+static int batch_sweep16_k(const ElimDesc *D, const int *idx, const int *pre, int nact, int total, int b,
+                           cudaStream_t s)
 {
-    if (nact <= 0 || total <= 0)
-        return GF2_OK;
     static std::atomic<unsigned long long> attr_devs{0};
     if (attr_needed(attr_devs)) {
-        cudaError_t err = cudaFuncSetAttribute(k_sweep16_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
+        cudaError_t err =
+            cudaFuncSetAttribute(k_sweep16_b<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM);
         if (err != cudaSuccess)
             return note_cuda(err);
         attr_done(attr_devs);
     }
     const int tok = prof_begin(s);
-    k_sweep16_b<<<total, NT, SWEEP_SMEM, s>>>(D, idx, pre, nact, b);
+    k_sweep16_b<KB><<<total, NT, SWEEP_SMEM, s>>>(D, idx, pre, nact, b);
     prof_end(s, GF2_PROF_SWEEP, tok);
     prof_launched(1);
     return note_cuda(cudaGetLastError());
+}
+
+int batch_sweep16(const ElimDesc *D, const int *idx, const int *pre, int nact, int total, int b, int k, cudaStream_t s)
+{
+    if (nact <= 0 || total <= 0)
+        return GF2_OK;
+    return k == 4 ? batch_sweep16_k<4>(D, idx, pre, nact, total, b, s) : batch_sweep16_k<8>(D, idx, pre, nact, total, b, s);
 }
 
 int launch_sweep16(const Elim &e, int b, cudaStream_t s)
 {
     if (e.mode && !e.ups)
         return GF2_EINVAL;
-    return e.mode == 2 ? launch<2>(e, b, s) : e.mode == 1 ? launch<1>(e, b, s) : launch<0>(e, b, s);
+    if (e.mode == 2)
+        return launch<2, 8>(e, b, s);
+    if (e.mode == 1)
+        return launch<1, 8>(e, b, s);
+    return e.k == 4 ? launch<0, 4>(e, b, s) : launch<0, 8>(e, b, s);
 }
 
 }  // namespace gf2

@@ -64,12 +64,32 @@ __device__ __forceinline__ u64 coords(const SweepSmem &S, const Lanes &L, u64 wv
     return z;
 }
 
-// x[0..3] = (z.O) at this thread's 4 words of the tile: 8 half-table rows and 1 top-bit row
+// x[0..3] = (z.O) at this thread's 4 words of the tile. KB = 8: 8 half-table rows and 1 top-bit
+// row; KB = 4: 16 rows of 16-entry tables.
+template <int KB>
 __device__ __forceinline__ void lookup(const Lanes &L, u64 z, u64 (&x)[4])
 {
     const int h1 = L.odd ? 2 : 0, h2 = 2 - h1;
     const unsigned zl = (unsigned)z, zh = (unsigned)(z >> 32);
     u64 p0 = 0, p1 = 0, q0 = 0, q1 = 0;
+    if (KB == 4) {
+#pragma unroll
+        for (int g = 0; g < 16; ++g) {
+            const unsigned v = ((g < 8 ? zl : zh) >> (4 * (g & 7))) & 15u;
+            const u64 *e = L.Tb + (g * 16 + (int)v) * TW;
+            const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(e + h1);
+            const ulonglong2 c = *reinterpret_cast<const ulonglong2 *>(e + h2);
+            p0 ^= a.x;
+            p1 ^= a.y;
+            q0 ^= c.x;
+            q1 ^= c.y;
+        }
+        x[0] = L.odd ? q0 : p0;
+        x[1] = L.odd ? q1 : p1;
+        x[2] = L.odd ? p0 : q0;
+        x[3] = L.odd ? p1 : q1;
+        return;
+    }
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
         const unsigned v = ((g < 4 ? zl : zh) >> (8 * (g & 3))) & 127u;
@@ -133,7 +153,7 @@ __device__ __forceinline__ void prefetch_l2(const void *p)
 // holds the panel word b, word b + 1 or words past W, so threads with such words store per word.
 // Pipeline: physical row 5 blocks ahead, an L2 prefetch of the row's 128-byte line 4 ahead, the
 // panel word 3 ahead, the row data 2 ahead (registers), then the block itself.
-template <int MODE, bool UP, bool EDGE, bool COUNT>
+template <int MODE, bool UP, bool EDGE, bool COUNT, int KB>
 __device__ __forceinline__ void lean_blocks(const Cfg &c, const SweepSmem &S, const Lanes &L, int w0, int ja, int jb,
                                             unsigned long long &cnt)
 {
@@ -182,7 +202,7 @@ __device__ __forceinline__ void lean_blocks(const Cfg &c, const SweepSmem &S, co
             const int p = pbase + j * RPU;
             const u64 z = coords(S, L, wv0);
             u64 x[4];
-            lookup(L, z, x);
+            lookup<KB>(L, z, x);
             if (p < c.m && !idle && (wv0 != 0 || EDGE)) {
                 uint64_t *row = UP ? c.out + (int64_t)p * c.ostride : c.A + (int64_t)ph0 * c.stride;
                 u64 nw[4];
@@ -246,7 +266,7 @@ __device__ __forceinline__ int row_code(const Cfg &c, int p)
 }
 
 // One block of any tile, any rows (pivot rows, window rows, the panel word's tile).
-template <int MODE, bool COUNT>
+template <int MODE, bool COUNT, int KB>
 __device__ __forceinline__ void general_block(const Cfg &c, const SweepSmem &S, const Lanes &L, int w0, int j,
                                               unsigned long long &cnt)
 {
@@ -268,7 +288,7 @@ __device__ __forceinline__ void general_block(const Cfg &c, const SweepSmem &S, 
     if (code <= -3)
         z = MODE ? c.st->zmap[c.st->pcol[-3 - code]] : c.st->zpiv[-3 - code];
     u64 x[4];
-    lookup(L, z, x);
+    lookup<KB>(L, z, x);
     if (code == CODE_NONE)
         return;
 #pragma unroll
@@ -301,7 +321,7 @@ __device__ __forceinline__ void general_block(const Cfg &c, const SweepSmem &S, 
 }
 
 // The sweep proper (the panel has pivots): tables per tile, then the blocks of each tile.
-template <int MODE, bool COUNT>
+template <int MODE, bool COUNT, int KB>
 __device__ __forceinline__ void sweep_body(Cfg &c, SweepSmem &S, unsigned long long &cnt, int cta, int ncta)
 {
     c.row0 = MODE ? 0 : c.r;
@@ -381,43 +401,53 @@ __device__ __forceinline__ void sweep_body(Cfg &c, SweepSmem &S, unsigned long l
             S.O[e] = v;
         }
         __syncthreads();
-        for (int e = tid; e < 8 * 8 * TW; e += NT) {
-            // group g, high bits vh (rows 8 g + 4 .. 8 g + 6), word wi: 16 entries by Gray code
-            const int wi = e % TW, vh = (e / TW) & 7, g = e / (8 * TW);
-            const u64 *Og = S.O + (8 * g) * TW + wi;
-            u64 base = 0;
-#pragma unroll
-            for (int bit = 0; bit < 3; ++bit)
-                base ^= ((vh >> bit) & 1) ? Og[(4 + bit) * TW] : 0ull;
-            gray16(base, Og[0], Og[TW], Og[2 * TW], Og[3 * TW], S.T + (g * 128 + (vh << 4)) * TW + wi, TW);
+        if (KB == 4) {
+            // 16 tables of the 16 sums of 4 pivot rows each
+            for (int e = tid; e < 16 * TW; e += NT) {
+                const int wi = e % TW, g = e / TW;
+                const u64 *Og = S.O + (4 * g) * TW + wi;
+                gray16(0ull, Og[0], Og[TW], Og[2 * TW], Og[3 * TW], S.T + (g * 16) * TW + wi, TW);
+            }
+            __syncthreads();
+        } else {
+            for (int e = tid; e < 8 * 8 * TW; e += NT) {
+                // group g, high bits vh (rows 8 g + 4 .. 8 g + 6), word wi: 16 entries by Gray code
+                const int wi = e % TW, vh = (e / TW) & 7, g = e / (8 * TW);
+                const u64 *Og = S.O + (8 * g) * TW + wi;
+                u64 base = 0;
+    #pragma unroll
+                for (int bit = 0; bit < 3; ++bit)
+                    base ^= ((vh >> bit) & 1) ? Og[(4 + bit) * TW] : 0ull;
+                gray16(base, Og[0], Og[TW], Og[2 * TW], Og[3 * TW], S.T + (g * 128 + (vh << 4)) * TW + wi, TW);
+            }
+            if (tid < 16 * TW) {
+                const int wi = tid % TW, vh = tid / TW;
+                const u64 *O7 = S.O + 7 * TW + wi;  // row 8 g + 7 at O7[8 g TW]
+                u64 base = 0;
+    #pragma unroll
+                for (int bit = 0; bit < 4; ++bit)
+                    base ^= ((vh >> bit) & 1) ? O7[8 * (4 + bit) * TW] : 0ull;
+                gray16(base, O7[0], O7[8 * TW], O7[16 * TW], O7[24 * TW], S.U + (vh << 4) * TW + wi, TW);
+            }
+            __syncthreads();
         }
-        if (tid < 16 * TW) {
-            const int wi = tid % TW, vh = tid / TW;
-            const u64 *O7 = S.O + 7 * TW + wi;  // row 8 g + 7 at O7[8 g TW]
-            u64 base = 0;
-#pragma unroll
-            for (int bit = 0; bit < 4; ++bit)
-                base ^= ((vh >> bit) & 1) ? O7[8 * (4 + bit) * TW] : 0ull;
-            gray16(base, O7[0], O7[8 * TW], O7[16 * TW], O7[24 * TW], S.U + (vh << 4) * TW + wi, TW);
-        }
-        __syncthreads();
         const int w0 = wbase + 4 * L.sub;
         const bool interior = wbase >= b + 2 && wbase + TW <= W;
         const int ua = blk0, ub = min(blk1, up_end);
         if (MODE && ua < ub) {
             if (interior)
-                lean_blocks<MODE, true, false, COUNT>(c, S, L, w0, ua, ub, cnt);
+                lean_blocks<MODE, true, false, COUNT, KB>(c, S, L, w0, ua, ub, cnt);
             else
-                lean_blocks<MODE, true, true, COUNT>(c, S, L, w0, ua, ub, cnt);
+                lean_blocks<MODE, true, true, COUNT, KB>(c, S, L, w0, ua, ub, cnt);
         }
         for (int j = max(blk0, up_end); j < min(blk1, plain_blk); ++j)
-            general_block<MODE, COUNT>(c, S, L, w0, j, cnt);
+            general_block<MODE, COUNT, KB>(c, S, L, w0, j, cnt);
         const int ta = max(blk0, plain_blk);
         if (ta < blk1) {
             if (interior)
-                lean_blocks<MODE, false, false, COUNT>(c, S, L, w0, ta, blk1, cnt);
+                lean_blocks<MODE, false, false, COUNT, KB>(c, S, L, w0, ta, blk1, cnt);
             else
-                lean_blocks<MODE, false, true, COUNT>(c, S, L, w0, ta, blk1, cnt);
+                lean_blocks<MODE, false, true, COUNT, KB>(c, S, L, w0, ta, blk1, cnt);
         }
     }
 }
@@ -426,7 +456,7 @@ __device__ __forceinline__ void sweep_body(Cfg &c, SweepSmem &S, unsigned long l
 // One panel's sweep by CTAs cta of ncta. FORM 0: PLS; 1: reduced echelon form; 2: hybrid, the
 // form the pivot search chose for this panel (st->mode), and the set bits of the trailing rows'
 // next panel word are counted into st->pop.
-template <int FORM>
+template <int FORM, int KB>
 __device__ __forceinline__ void sweep_panel16(SweepSmem &S, uint64_t *__restrict__ A, int64_t stride,
                                               const u64 *__restrict__ side_cur, u64 *__restrict__ side_nxt,
                                               const int *__restrict__ perm, const PanelState *__restrict__ st,
@@ -484,9 +514,9 @@ __device__ __forceinline__ void sweep_panel16(SweepSmem &S, uint64_t *__restrict
         if (__syncthreads_or(nzw) && tid == 0)
             atomicExch(const_cast<int *>(&st->nz), 1);
     } else if (!reduced) {
-        sweep_body<0, FORM == 2>(c, S, cnt, cta, ncta);
+        sweep_body<0, FORM == 2, KB>(c, S, cnt, cta, ncta);
     } else {
-        sweep_body<1, FORM == 2>(c, S, cnt, cta, ncta);
+        sweep_body<1, FORM == 2, 8>(c, S, cnt, cta, ncta);  // the reduced form is built for k = 8
     }
     if (FORM == 2) {
         // the density count for the hybrid's switch

@@ -102,6 +102,11 @@ extern "C" int gf2_autotune(int op, int64_t m, int64_t n, double density, gf2_op
     } else {
         for (int tw : {4, 8, 16})
             cands.push_back(opt(tw, 0, 0));
+        {
+            gf2_opts o = opt(16, 0, 0);  // 4-bit tables (Sec. 3.1's k) on the 16-word sweep
+            o.k = 4;
+            cands.push_back(o);
+        }
         if (op == GF2_OP_RREF) {
             // the direct reduced form (M4RI, Sec. 3.1) and the hybrid at the paper's two thresholds
             for (int meth : {GF2_RREF_M4RI, GF2_RREF_HYBRID}) {

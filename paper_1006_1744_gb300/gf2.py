@@ -63,6 +63,7 @@ SYMBOLS = {
     "gf2_rank_noalloc": (_int, [_vp, _i64, _i64, _i64, _vp, _vp]),
     "gf2_pls_batched_workspace_bytes": (_sz, [_vp, _i64, _vp]),
     "gf2_pls_batched": (_int, [_vp, _i64, _vp, _vp, _sz, _vp, _vp]),
+    "gf2_batch_plan": (_int, [_vp, _i64, _int, _vp, _vp, _vp]),
     "gf2_autotune": (_int, [_int, _i64, _i64, ctypes.c_double, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_double), _vp]),
     "gf2_sync_status": (_int, [_vp]),
     "gf2_diag_wait_timeout": (_int, [ctypes.c_uint64, _vp]),
@@ -277,6 +278,21 @@ def pls_batched_workspace_bytes(shapes, opts=None) -> int:
     return int(lib().gf2_pls_batched_workspace_bytes(items, len(shapes), _opts(opts)))
 
 
+def batch_plan(shapes, ctas: int):
+    """Host-only plan of the persistent batched schedule for (m, n) shapes on `ctas` CTAs.
+    Returns (team_of per CTA, team sizes, team per matrix); -1 marks queue CTAs / queued matrices."""
+    items = (BatchItem * max(1, len(shapes)))()
+    for i, (m, n) in enumerate(shapes):
+        items[i] = BatchItem(None, m, n, max(16, ((n + 63) // 64 + 15) // 16 * 16), None, None)
+    team_of = (ctypes.c_int * max(1, ctas))()
+    team_size = (ctypes.c_int * max(1, ctas))()
+    member = (ctypes.c_int * max(1, len(shapes)))()
+    nt = lib().gf2_batch_plan(items, len(shapes), ctas, team_of, team_size, member)
+    if nt < 0:
+        raise Gf2Error(1, "gf2_batch_plan")
+    return list(team_of)[:ctas], list(team_size)[:nt], list(member)[:len(shapes)]
+
+
 def pls_batched(mats, ns, Ps=None, Qs=None, ranks=None, work=None, opts=None, stream=None):
     """PLS of every matrix in `mats` (in place) in one batched call.
     Returns (Ps, Qs, ranks) with ranks a device int64 tensor of length len(mats)."""
@@ -300,5 +316,5 @@ def autotune(op: int, m: int, n: int, density: float = 0.5, stream=None):
     ms = ctypes.c_double(0.0)
     _check(lib().gf2_autotune(op, m, n, float(density), ctypes.byref(best), ctypes.byref(ms), _stream(stream)),
            "gf2_autotune")
-    return {"tile_words": best.tile_words, "cutoff_cols": best.cutoff_cols, "product": best.product,
+    return {"k": best.k, "tile_words": best.tile_words, "cutoff_cols": best.cutoff_cols, "product": best.product,
             "rref_method": best.rref_method, "hybrid_permille": best.hybrid_permille}, ms.value

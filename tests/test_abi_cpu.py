@@ -79,6 +79,19 @@ def test_argument_checks_reject_before_any_device_work(built):
     bad = gf2.Opts()
     bad.reserved[2] = 1
     assert L.gf2_rref(fake, 8, 8, 16, rank, None, None, 0, ctypes.byref(bad), None) == EINVAL
+    # table width: 4 and 8 only; 4 only on the 16-word PLS-form sweep
+    for k, extra in [(6, {}), (16, {}), (4, {"rref_method": 2}), (4, {"rref_method": 3}), (4, {"tile_words": 8}),
+                     (4, {"batch_mode": 2})]:
+        bad = gf2.Opts()
+        bad.k = k
+        for f, v in extra.items():
+            setattr(bad, f, v)
+        assert L.gf2_rref(fake, 8, 8, 16, rank, None, None, 0, ctypes.byref(bad), None) == EINVAL, (k, extra)
+    # route and schedule codes
+    for f, v in [("rref_method", 4), ("rref_method", -1), ("hybrid_permille", 1001), ("batch_mode", 3)]:
+        bad = gf2.Opts()
+        setattr(bad, f, v)
+        assert L.gf2_rref(fake, 8, 8, 16, rank, None, None, 0, ctypes.byref(bad), None) == EINVAL, (f, v)
     assert L.gf2_rank(fake, 8, 8, 16, None, None, 0, None, None) == EINVAL
     # misaligned or undersized caller workspace
     assert L.gf2_pls(fake, 8, 8, 16, P, Q, rank, fake + 64, 1 << 30, None, None) == EALIGN

@@ -74,6 +74,33 @@ def test_pls_parity_tile_and_grid_choices(g, tile):
         check_pls(g, A, 600, 900, opts={"tile_words": tile, "grid_ctas": grid})
 
 
+@pytest.mark.parametrize("kind", KINDS)
+def test_k4_tables_parity(g, kind):
+    """Four-bit Gray-code tables (k = 4: sixteen tables of 16 entries per sweep) give
+    the same PLS, rank and RREF (PLS route) as the oracle, alone and batched."""
+    o = {"k": 4}
+    for i, (m, n) in enumerate([(1, 1), (65, 65), (129, 300), (700, 500), (1024, 1024), (1300, 2100)]):
+        A = make(kind, m, n, 4100 + i)
+        check_pls(g, A, m, n, opts=o)
+        D = dev(A)
+        assert int(g.rank(D, n, opts=o).item()) == oracle.rank(A, m, n)
+        R, piv, r = oracle.rref(A, m, n)
+        rd, pd = g.rref(D, n, opts=o)
+        torch.cuda.synchronize()
+        W = S.words_per_row(n)
+        assert int(rd.item()) == r and (pd.cpu().numpy()[:r] == piv).all()
+        assert (host(D)[:, :W] == R[:, :W]).all()
+    hosts = [(make(kind, m, n, 4200 + i), m, n) for i, (m, n) in enumerate([(300, 200), (129, 700), (2000, 300)])]
+    ds = [dev(A) for (A, _, _) in hosts]
+    Ps, Qs, ranks = g.pls_batched(ds, [n for (_, _, n) in hosts], opts={"k": 4, "batch_mode": g.BATCH_STEPS})
+    torch.cuda.synchronize()
+    for i, (A, m, n) in enumerate(hosts):
+        R, P, Q, r = oracle.pls(A, m, n)
+        assert int(ranks[i].item()) == r
+        assert (Ps[i].cpu().numpy()[:m] == P[:m]).all() and (Qs[i].cpu().numpy()[:n] == Q[:n]).all()
+        assert (host(ds[i])[:, :S.words_per_row(n)] == R[:, :S.words_per_row(n)]).all()
+
+
 def test_pls_parity_wide_stride_and_user_workspace(g):
     m, n = 300, 500
     A = S.dense(m, n, 5, stride=48)
