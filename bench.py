@@ -637,7 +637,12 @@ def run_headline(args):
     with_rref = args.config in (1, 2)
     W = (n + 63) // 64
     stride = max(16, (W + 15) // 16 * 16)
-    opts = {"tile_words": args.tile_words} if args.tile_words else None
+    opts = {}
+    if args.tile_words:
+        opts["tile_words"] = args.tile_words
+    if args.panels_per_sweep:
+        opts["panels_per_sweep"] = args.panels_per_sweep
+    opts = opts or None
     big = m * stride * 8 > 256 * 1024 * 1024  # input larger than L2: no flush needed
 
     A0 = torch.empty((m, stride), dtype=torch.int64, device=dev)
@@ -834,6 +839,8 @@ def main():
     ap.add_argument("--impl", default="gf2", choices=["gf2", "reference"])
     ap.add_argument("--n", type=int, default=0, help="matrix size of the headline form (default: by config)")
     ap.add_argument("--tile-words", type=int, default=0)
+    ap.add_argument("--panels-per-sweep", type=int, default=0, choices=[0, 1, 2],
+                    help="panels per table sweep of the PLS elimination (0: the library's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-side", action="store_true", help="config 3: skip the 16384^2 side figures")

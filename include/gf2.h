@@ -93,7 +93,11 @@ typedef struct gf2_opts {
     int hybrid_permille;/* GF2_RREF_HYBRID: switch to PLS once the remaining rows' density reaches this many
                            per mille (Sec. 6, "M+P 0.15"; 0 = 150) */
     int batch_mode;     /* gf2_pls_batched: GF2_BATCH_* (0 = GF2_BATCH_AUTO) */
-    int reserved[5];    /* must be zero */
+    int panels_per_sweep;/* MMPF in PLS form (gf2_pls, gf2_rank, gf2_rref's PLS route): 1 = one table sweep of
+                           the trailing block per 64-column panel; 2 = the pivots of two panels first, then one
+                           sweep for both (half the trailing block's DRAM traffic); 0 = the library's choice.
+                           Same results either way. Ignored by the reduced-form RREF routes and the batch */
+    int reserved[4];    /* must be zero */
 } gf2_opts;
 
 /* schedules of gf2_pls_batched (same results) */
@@ -354,7 +358,8 @@ int gf2_version(void);
 #define GF2_PROF_PIVOT 1 /* pivot search of a panel (PlsSubmatrix) */
 #define GF2_PROF_RREF 2  /* one 64-pivot block of the RREF back substitution */
 #define GF2_PROF_MUL 3   /* product kernels */
-#define GF2_PROF_CLASSES 4
+#define GF2_PROF_COORDS 4 /* coordinates and multipliers of the rows of a two-panel sweep step */
+#define GF2_PROF_CLASSES 5
 void gf2_prof_enable(int flags);
 void gf2_prof_reset(void);
 long long gf2_prof_launches(void);

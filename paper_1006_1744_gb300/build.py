@@ -25,7 +25,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompil
               "-I" + os.path.join(ROOT, "include")] + ARCH
 
 LIBS = {
-    "libgf2.so": ["gf2_api.cu", "gf2_pls.cu", "gf2_rref.cu", "gf2_mul.cu", "gf2_mul_tc.cu", "gf2_prof.cu", "gf2_noalloc.cu", "gf2_rec.cu", "gf2_status.cu", "gf2_batch.cu", "gf2_tune.cu", "gf2_graph.cu", "gf2_strassen.cu", "gf2_sweep.cu"],
+    "libgf2.so": ["gf2_api.cu", "gf2_pls.cu", "gf2_rref.cu", "gf2_mul.cu", "gf2_mul_tc.cu", "gf2_prof.cu", "gf2_noalloc.cu", "gf2_rec.cu", "gf2_status.cu", "gf2_batch.cu", "gf2_tune.cu", "gf2_graph.cu", "gf2_strassen.cu", "gf2_sweep.cu", "gf2_pair.cu"],
     "libgf2synth.so": ["gf2_synth.cu"],
 }
 

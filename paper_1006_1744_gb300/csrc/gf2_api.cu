@@ -43,7 +43,7 @@ ElimLayout elim_layout(int op, int64_t m, int64_t n)
     const int64_t stride = min_stride(n);
     size_t off = 0;
     L.state = off;
-    off = align_up(off + 2 * sizeof(PanelState), 256);
+    off = align_up(off + 4 * sizeof(PanelState), 256);  // two slots, or four for two panels per sweep
     L.perm = off;
     off = align_up(off + (size_t)m * sizeof(int), 256);
     L.side = off;
@@ -161,7 +161,9 @@ int check_opts(const gf2_opts *o)
         return GF2_EINVAL;
     if (o->batch_mode < 0 || o->batch_mode > GF2_BATCH_PERSISTENT)
         return GF2_EINVAL;
-    for (int i = 0; i < 5; ++i)
+    if (o->panels_per_sweep < 0 || o->panels_per_sweep > 2)
+        return GF2_EINVAL;
+    for (int i = 0; i < 4; ++i)
         if (o->reserved[i])
             return GF2_EINVAL;
     return GF2_OK;
@@ -191,6 +193,9 @@ static Elim make_elim(uint64_t *A, int64_t m, int64_t n, int64_t stride, char *w
     e.mode = 0;
     e.hybrid_permille = o ? o->hybrid_permille : 0;
     e.k = (o && o->k) ? o->k : 8;
+    e.pps = (o && o->panels_per_sweep) ? o->panels_per_sweep : 1;
+    if (e.pps == 2)
+        e.stf = e.W > 0 ? e.st + ((e.W - 1) & 3) : e.st;  // panel b's state lives in slot b & 3
     // default: one CTA per SM but one, so the look-ahead pivot search (which cannot share an
     // SM with a 1024-thread sweep CTA) never holds back a CTA of the sweep it overlaps
     const int nsm = sm_count();
@@ -240,7 +245,7 @@ static CallKey call_key(int op, const void *A, int64_t m, int64_t n, int64_t str
     cudaGetDevice(&k.device);
     k.op = op;
     k.tile_words = e.tile_words;
-    k.grid = e.grid + (e.k << 27);  // the table width changes the launches too
+    k.grid = e.grid + (e.k << 27) + (e.pps << 24);  // the table width and panels per sweep change the launches too
     k.A = A;
     k.m = m;
     k.n = n;
@@ -340,6 +345,10 @@ int gf2_rref(uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *rank, i
     e.ups = reinterpret_cast<u64 *>(w + L.ups);
     if (e.mode && e.tile_words != 16)
         return GF2_EINVAL;  // the reduced form is built on the 16-word sweep only
+    if (e.mode && e.pps != 1) {
+        e.pps = 1;  // the reduced form sweeps one panel at a time
+        e.stf = final_state(e.st, e.W);
+    }
     CallKey key = call_key(GF2_OP_RREF + 16 * e.mode, A, m, n, stride, nullptr, nullptr, rank, pivots, work,
                            work_bytes, e);
     key.grid += e.hybrid_permille << 16;  // the threshold changes the launches' behaviour

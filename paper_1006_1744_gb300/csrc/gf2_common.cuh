@@ -266,6 +266,7 @@ struct Elim {
                       // 2 = hybrid (reduced form until the density reaches hybrid_permille, then PLS)
     int hybrid_permille;
     int k;            // bits per Gray-code table of the 16-word PLS-form sweep: 8 or 4
+    int pps;          // panels per table sweep (PLS form): 1, or 2 (gf2_pair.cu: state slots b & 3)
 };
 
 // One matrix of a batched elimination (device-resident array, one per matrix).
@@ -317,6 +318,9 @@ struct ElimAux {
     cudaEvent_t ev[3];
 };
 int elim_run(const Elim &e, const ElimAux &aux);
+// two panels per sweep (gf2_pair.cu), and the pieces of gf2_pls.cu it uses
+int elim_run_pair(const Elim &e, const ElimAux &aux);
+int apply_final_order(const Elim &e);
 // rank of A (unchanged) by a direct elimination of a copy in work (gf2_api.cu): never replayed
 // from a graph, allocates nothing
 int rank_direct(const uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *rank, char *work,

@@ -1,0 +1,578 @@
+// gf2_pair.cu -- MMPF elimination with two panels per table sweep.
+//
+// The one-panel pipeline (gf2_pls.cu, gf2_sweep.cu) reads and writes the whole
+// trailing block once per 64-column panel. Here the pivots of panels b and
+// b + 1 (b even) are found first and the trailing block is then swept once for
+// both (AddRowsFromTable of Sec. 3.1 / 4.1 over 128 pivot columns), which halves
+// the DRAM traffic of the sweeps and keeps their shared-memory lookups per panel
+// the same:
+//   * k_pivot_pair (gf2_pls.cu): the pivots of panel b (A's word b is current),
+//     then of panel c = b + 1 (A's word b + 1 plus panel b's contribution, the
+//     look-ahead of the one-panel pipeline), panel b's row order left out of
+//     perm while the previous sweep still reads it;
+//   * k_pair_coords: the coordinates z_b of every row below panel b's pivots over
+//     panel b's pivot rows O_b, and z_c of every row below both panels' pivots
+//     over O_c (panel c's pivot rows after panel b), from its words b and b + 1;
+//     it writes the multipliers of L into words b and b + 1, the pivot rows'
+//     final words b and b + 1 into `out`, and panel b's row order into perm;
+//   * k_pair_sweep: MakeTable1 for both panels on 8-word column tiles, O_c formed
+//     from O_b's tables, and row ^= z_b.O_b ^ z_c.O_c on every trailing row from
+//     word b + 2 on. One 128-byte line of shared memory holds entry v of both
+//     panels' tables; the two rows of a quarter-warp read opposite halves of
+//     their lines, so every lookup instruction is free of bank conflicts. The two
+//     CTAs of a pair take the two halves of the same 128-byte lines of the same
+//     rows, so each line is fetched from DRAM once.
+// A pair's sweep is two launches: words b + 2 and b + 3 first (all the next
+// pair's pivot searches read), then the rest, during which those searches run.
+// Every result equals the one-panel pipeline's, hence the Gaussian PLS's.
+#include <climits>
+
+#include "gf2_common.cuh"
+
+namespace {
+
+constexpr int NT = 512;          // threads per CTA
+constexpr int TPR = 4;           // threads per row, two words each
+constexpr int RPU = NT / TPR;    // rows per block (128)
+constexpr int LW = 16;           // words per table line: 8 of panel b's entry, 8 of panel c's
+constexpr int NLINE = 8 * 128 + 256;  // 8 half tables of 128 entries, one table of the groups' top rows
+
+struct PairSmem {
+    u64 T[NLINE * LW];
+    u64 Ob[64 * 8], Oc[64 * 8];  // pivot rows of the current tile (Oc: after panel b)
+    u64 zpb[64], zpc[64];        // pivot t -> its final row's coordinates (row t of L^-1)
+    int prb[64], prc[64];        // physical rows of the pivots
+};
+
+struct PairArgs {
+    uint64_t *A;
+    int64_t stride;
+    const int *perm;
+    const PanelState *sb, *sc;
+    const u64 *zb, *zc;  // per physical row: coordinates over O_b, over O_c
+    uint64_t *out;
+    int64_t ostride;
+    int m, W, b, wlo, whi, paired;
+};
+
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// bits 7, 15, ..., 63 of z gathered into one byte
+__device__ __forceinline__ unsigned top8(u64 z)
+{
+    const unsigned lo = (unsigned)z, hi = (unsigned)(z >> 32);
+    return ((((lo >> 7) & 0x01010101u) * 0x01020408u) >> 24) | (((((hi >> 7) & 0x01010101u) * 0x01020408u) >> 24) << 4);
+}
+
+// (z_b.O_b ^ z_c.O_c) at this thread's two words. Even rows read their panel-b half first,
+// odd rows their panel-c half: in each instruction the two rows of a quarter-warp touch
+// opposite halves of their lines.
+__device__ __forceinline__ void lookup2(const u64 *__restrict__ T, int sub, int odd, u64 zb, u64 zc, u64 &x0, u64 &x1)
+{
+    const int ob = 2 * sub, oc = 8 + 2 * sub;
+    u64 a0 = 0, a1 = 0;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        const int vb = (int)((zb >> (8 * g)) & 127u), vc = (int)((zc >> (8 * g)) & 127u);
+        const int lb = (g * 128 + vb) * LW + ob, lc = (g * 128 + vc) * LW + oc;
+        const ulonglong2 p = *reinterpret_cast<const ulonglong2 *>(T + (odd ? lc : lb));
+        const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(T + (odd ? lb : lc));
+        a0 ^= p.x ^ q.x;
+        a1 ^= p.y ^ q.y;
+    }
+    {
+        const int lb = (1024 + (int)top8(zb)) * LW + ob, lc = (1024 + (int)top8(zc)) * LW + oc;
+        const ulonglong2 p = *reinterpret_cast<const ulonglong2 *>(T + (odd ? lc : lb));
+        const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(T + (odd ? lb : lc));
+        a0 ^= p.x ^ q.x;
+        a1 ^= p.y ^ q.y;
+    }
+    x0 = a0;
+    x1 = a1;
+}
+
+// word wi of z.O_b, from panel b's tables (one word, for forming O_c)
+__device__ __forceinline__ u64 lookup_b1(const u64 *__restrict__ T, u64 z, int wi)
+{
+    u64 a = 0;
+#pragma unroll
+    for (int g = 0; g < 8; ++g)
+        a ^= T[(g * 128 + (int)((z >> (8 * g)) & 127u)) * LW + wi];
+    return a ^ T[(1024 + (int)top8(z)) * LW + wi];
+}
+
+// MakeTable1 of one panel's 64 pivot rows O (8 words each) into half h of every line, words
+// [va, vb) of the tile: group g's entry v < 128 sums rows 8 g + bit of v; the top table's
+// entry v sums rows 8 g + 7 for the set bits g of v. Gray-code order, one XOR per entry.
+__device__ __forceinline__ void build_tables(u64 *__restrict__ T, const u64 *__restrict__ O, int h, int va, int vb)
+{
+    const int tid = threadIdx.x, nw = vb - va;
+    if (nw <= 0)
+        return;
+    for (int e = tid; e < 8 * 8 * nw; e += NT) {
+        const int wi = va + e % nw, vh = (e / nw) & 7, g = e / (8 * nw);
+        const u64 *Og = O + (8 * g) * 8 + wi;
+        u64 base = 0;
+#pragma unroll
+        for (int bit = 0; bit < 3; ++bit)
+            base ^= ((vh >> bit) & 1) ? Og[(4 + bit) * 8] : 0ull;
+        gray16(base, Og[0], Og[8], Og[16], Og[24], T + (g * 128 + (vh << 4)) * LW + 8 * h + wi, LW);
+    }
+    for (int e = tid; e < 16 * nw; e += NT) {
+        const int wi = va + e % nw, vh = e / nw;
+        const u64 *O7 = O + 7 * 8 + wi;  // row 8 g + 7 at O7[64 g]
+        u64 base = 0;
+#pragma unroll
+        for (int bit = 0; bit < 4; ++bit)
+            base ^= ((vh >> bit) & 1) ? O7[64 * (4 + bit)] : 0ull;
+        gray16(base, O7[0], O7[64], O7[128], O7[192], T + (1024 + (vh << 4)) * LW + 8 * h + wi, LW);
+    }
+}
+
+struct PairRows {
+    int R0, R1, R2;      // panel b's pivots at [R0, R1), panel c's at [R1, R2), trailing rows from R2
+    int nwin, nx;        // panel c's window and swaps past it
+    int plain_from;      // positions from here on are perm[p] alone
+};
+
+// Pipelined sweep of blocks [ja, jb) of trailing rows given by perm alone. Per thread: the
+// physical row 5 blocks ahead, an L2 prefetch of its tile 4 ahead, its coordinates 3 ahead,
+// its two words 2 ahead.
+__device__ __forceinline__ void pair_plain(const PairArgs &a, const PairSmem &S, const PairRows &R, int sub, int rg,
+                                           int odd, int w0, bool v0, bool v1, int ja, int jb, bool check, bool &nzw)
+{
+    const int pbase = R.R0 + rg, plast = a.m - 1;
+    const bool idle = !v0 && !v1, both = v0 && v1;
+    auto pos = [&](int jj) { return min(max(pbase + jj * RPU, 0), plast); };
+    int ph0 = 0, ph1 = 0, ph2 = 0, ph3 = 0, ph4 = 0, ph5 = 0;
+    u64 zb0 = 0, zb1 = 0, zb2 = 0, zb3 = 0, zc0 = 0, zc1 = 0, zc2 = 0, zc3 = 0;
+    u64 d00 = 0, d01 = 0, d10 = 0, d11 = 0, d20 = 0, d21 = 0;
+    for (int j = ja - 5; j < jb; ++j) {
+        ph5 = a.perm[pos(j + 5)];
+        if (!idle)
+            prefetch_l2(a.A + (int64_t)ph4 * a.stride + w0);
+        zb3 = a.zb[ph3];
+        zc3 = a.zc[ph3];
+        if (!idle && ((zb2 | zc2) != 0 || check)) {
+            const uint64_t *src = a.A + (int64_t)ph2 * a.stride + w0;
+            if (both) {
+                const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2 *>(src));
+                d20 = v.x;
+                d21 = v.y;
+            } else {
+                d20 = v0 ? src[0] : 0ull;
+                d21 = v1 ? src[1] : 0ull;
+            }
+        } else {
+            d20 = d21 = 0;
+        }
+        if (j >= ja) {
+            u64 x0, x1;
+            lookup2(S.T, sub, odd, zb0, zc0, x0, x1);
+            const int p = pbase + j * RPU;
+            if (p < a.m && !idle && ((zb0 | zc0) != 0 || check)) {
+                const u64 n0 = d00 ^ x0, n1 = d01 ^ x1;
+                if (check)
+                    nzw = nzw || (v0 && n0 != 0) || (v1 && n1 != 0);
+                if ((zb0 | zc0) != 0) {
+                    uint64_t *dst = a.A + (int64_t)ph0 * a.stride + w0;
+                    if (both) {
+                        ulonglong2 v;
+                        v.x = n0;
+                        v.y = n1;
+                        __stcs(reinterpret_cast<ulonglong2 *>(dst), v);
+                    } else {
+                        if (v0)
+                            dst[0] = n0;
+                        if (v1)
+                            dst[1] = n1;
+                    }
+                }
+            }
+        }
+        ph0 = ph1;
+        ph1 = ph2;
+        ph2 = ph3;
+        ph3 = ph4;
+        ph4 = ph5;
+        zb0 = zb1;
+        zb1 = zb2;
+        zb2 = zb3;
+        zc0 = zc1;
+        zc1 = zc2;
+        zc2 = zc3;
+        d00 = d10;
+        d01 = d11;
+        d10 = d20;
+        d11 = d21;
+    }
+}
+
+// One block of any rows: the pivot rows of both panels (their final rows go to `out`), the
+// window rows of panel c and rows it swapped from past its window.
+__device__ __forceinline__ void pair_general(const PairArgs &a, const PairSmem &S, const PairRows &R, int sub, int rg,
+                                             int odd, int w0, bool v0, bool v1, int j, bool check, bool &nzw)
+{
+    const int p = R.R0 + j * RPU + rg;
+    int kind = 0, ph = 0;  // 0 none, 1 pivot of b, 2 pivot of c, 3 trailing
+    u64 zb = 0, zc = 0;
+    if (p < a.m) {
+        if (p < R.R1) {
+            kind = 1;
+            zb = S.zpb[p - R.R0];
+        } else if (p < R.R2) {
+            kind = 2;
+            zc = S.zpc[p - R.R1];
+        } else {
+            kind = 3;
+            ph = trailing_row(a.perm, a.sc, R.R1, R.nwin, R.nx, p);
+            zb = a.zb[ph];
+            zc = a.zc[ph];
+        }
+    }
+    u64 x0, x1;
+    lookup2(S.T, sub, odd, zb, zc, x0, x1);
+    if (kind == 3) {
+        uint64_t *row = a.A + (int64_t)ph * a.stride + w0;
+        const u64 n0 = v0 ? row[0] ^ x0 : 0ull, n1 = v1 ? row[1] ^ x1 : 0ull;
+        if (check)
+            nzw = nzw || n0 != 0 || n1 != 0;
+        if (v0)
+            row[0] = n0;
+        if (v1)
+            row[1] = n1;
+    } else if (kind && a.out) {
+        uint64_t *row = a.out + (int64_t)p * a.ostride + w0;
+        if (v0)
+            row[0] = x0;
+        if (v1)
+            row[1] = x1;
+    }
+}
+
+__global__ void __launch_bounds__(NT, 1) k_pair_sweep(PairArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    PairSmem &S = *reinterpret_cast<PairSmem *>(smraw);
+    const int tid = threadIdx.x;
+    const PanelState *__restrict__ sb = a.sb, *__restrict__ sc = a.sc;
+    PairRows R;
+    R.R0 = sb->r_cur;
+    R.R1 = R.R0 + sb->kbar;
+    R.R2 = R.R1 + sc->kbar;
+    R.nwin = sc->nwin;
+    R.nx = sc->nx;
+    R.plain_from = R.nx ? INT_MAX : R.R1 + max(sc->kbar, R.nwin);
+    const int kb = sb->kbar, kc = sc->kbar;
+    // no pivot in panel c: look for a nonzero word right of it in any trailing row (none means
+    // no later panel has a pivot), unless that is known already
+    const bool check = kc == 0 && !sc->zero_tail;
+    bool nzw = false;
+    const int lo = max(a.wlo, a.b + 2), hi = min(a.whi, a.W);
+    const int M = a.m - R.R0;
+    if ((kb || kc || check) && M > 0 && lo < hi) {
+        if (tid < 64) {
+            S.prb[tid] = tid < kb ? sb->prow[tid] : 0;
+            S.prc[tid] = tid < kc ? sc->prow[tid] : 0;
+            S.zpb[tid] = tid < kb ? sb->zpiv[tid] : 0ull;
+            S.zpc[tid] = tid < kc ? sc->zpiv[tid] : 0ull;
+        }
+        const int nblk = (M + RPU - 1) / RPU;
+        const int plain_blk = R.plain_from == INT_MAX ? nblk : min(nblk, (R.plain_from - R.R0 + RPU - 1) / RPU);
+        // units: (tile, block) in tile-major order; paired: (128-byte line, block), the two CTAs of
+        // a pair taking the line's two tiles
+        const int half = a.paired ? (int)(blockIdx.x & 1) : 0;
+        const int team = a.paired ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+        const int nteam = a.paired ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+        const int c0 = a.paired ? (lo >> 4) : (lo >> 3), c1 = a.paired ? ((hi + 15) >> 4) : ((hi + 7) >> 3);
+        const long long total = (long long)(c1 - c0) * nblk;
+        const long long q_lo = total * team / nteam, q_hi = total * (team + 1) / nteam;
+        const int sub = tid & (TPR - 1), rg = tid / TPR, odd = (tid >> 2) & 1;
+        for (long long q = q_lo; q < q_hi;) {
+            const int col = (int)(q / nblk);
+            const long long q_end = min(q_hi, (long long)(col + 1) * nblk);
+            const int blk0 = (int)(q - (long long)col * nblk), blk1 = (int)(q_end - (long long)col * nblk);
+            q = q_end;
+            const int tile = a.paired ? 2 * (c0 + col) + half : c0 + col;
+            const int tb = 8 * tile;
+            const int va = max(lo, tb) - tb, vb = min(hi, tb + 8) - tb;
+            if (va >= vb)
+                continue;  // CTA-uniform: this half of the line holds no word to sweep
+            // ---- tables of this tile: panel b's, O_c from them, panel c's ----
+            __syncthreads();
+            for (int e = tid; e < 64 * 8; e += NT) {
+                const int t = e >> 3, wi = e & 7;
+                const bool in = wi >= va && wi < vb;
+                S.Ob[e] = in && t < kb ? a.A[(int64_t)S.prb[t] * a.stride + tb + wi] : 0ull;
+                S.Oc[e] = in && t < kc ? a.A[(int64_t)S.prc[t] * a.stride + tb + wi] : 0ull;
+            }
+            __syncthreads();
+            build_tables(S.T, S.Ob, 0, va, vb);
+            __syncthreads();
+            for (int e = tid; e < 64 * 8; e += NT) {
+                const int t = e >> 3, wi = e & 7;
+                if (t < kc && wi >= va && wi < vb)
+                    S.Oc[e] ^= lookup_b1(S.T, a.zb[S.prc[t]], wi);
+            }
+            __syncthreads();
+            build_tables(S.T, S.Oc, 1, va, vb);
+            __syncthreads();
+            const int w0 = tb + 2 * sub;
+            const bool v0 = w0 >= lo && w0 < hi, v1 = w0 + 1 >= lo && w0 + 1 < hi;
+            for (int j = blk0; j < min(blk1, plain_blk); ++j)
+                pair_general(a, S, R, sub, rg, odd, w0, v0, v1, j, check, nzw);
+            const int ta = max(blk0, plain_blk);
+            if (ta < blk1)
+                pair_plain(a, S, R, sub, rg, odd, w0, v0, v1, ta, blk1, check, nzw);
+        }
+    }
+    if (check && __syncthreads_or(nzw) && tid == 0) {
+        atomicExch(const_cast<int *>(&sb->nz), 1);
+        atomicExch(const_cast<int *>(&sc->nz), 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Coordinates of the rows of a pair, and the multipliers of L in its two panel words.
+// Byte tables (8 byte positions x 256 values) of five linear maps of a panel word:
+//   Zb: word b -> z_b (panel b's zmap), Xb: word b -> panel b's multipliers (z_b.X_b, X_t =
+//   pivot t's multipliers plus its own bit), Cb: word b -> panel b's contribution to word b + 1
+//   (z_b.O_b[b + 1]), and likewise Zc, Xc for panel c from word b + 1 after panel b.
+// ---------------------------------------------------------------------------
+constexpr int NMAP = 5;
+
+struct CoordSmem {
+    u64 tab[NMAP][8 * 256];
+    u64 img[NMAP][64];   // image of each bit of the panel word
+    u64 Xb[64], Xc[64], Ob1[64];
+};
+
+__device__ __forceinline__ u64 bytesum(const u64 *__restrict__ t, u64 w)
+{
+    u64 a = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        a ^= t[q * 256 + (int)((w >> (8 * q)) & 255u)];
+    return a;
+}
+
+__global__ void __launch_bounds__(NT, 1)
+k_pair_coords(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, const PanelState *__restrict__ sb,
+              const PanelState *__restrict__ sc, u64 *__restrict__ zb, u64 *__restrict__ zc,
+              uint64_t *__restrict__ out, int64_t ostride, int m, int W, int b)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    CoordSmem &S = *reinterpret_cast<CoordSmem *>(smraw);
+    const int tid = threadIdx.x;
+    const int kb = sb->kbar, kc = sc ? sc->kbar : 0;
+    const int R0 = sb->r_cur, R1 = R0 + kb, R2 = R1 + kc;
+    const bool has1 = b + 1 < W;  // word b + 1 exists
+    // panel b's row order into perm (its pivot search of panel c left it out): only positions
+    // that this kernel reads through sb, never through perm
+    if (sc) {
+        const int g = blockIdx.x * NT + tid, gs = gridDim.x * NT;
+        for (int i = g; i < sb->nwin; i += gs)
+            perm[R0 + i] = sb->wperm[i];
+        for (int x = g; x < sb->nx; x += gs)
+            perm[sb->xpos[x]] = sb->xval[x];
+    }
+    if (kb == 0 && kc == 0)
+        return;  // words b and b + 1 of every row below are zero already
+    if (tid < 64) {
+        const int t = tid;
+        S.Xb[t] = t < kb ? sb->newblk[t] & sb->J & lowmask(sb->pcol[t] + 1) : 0ull;
+        S.Ob1[t] = t < kb && has1 ? A[(int64_t)sb->prow[t] * stride + b + 1] : 0ull;
+        S.Xc[t] = t < kc ? sc->newblk[t] & sc->J & lowmask(sc->pcol[t] + 1) : 0ull;
+    }
+    __syncthreads();
+    if (tid < NMAP * 64) {
+        const int mp = tid >> 6, i = tid & 63;
+        const u64 zm = mp < 3 ? sb->zmap[i] : (sc ? sc->zmap[i] : 0ull);
+        u64 v = 0;
+        if (mp == 0 || mp == 3) {
+            v = zm;
+        } else {
+            const u64 *src = mp == 1 ? S.Xb : mp == 2 ? S.Ob1 : S.Xc;
+            for (int t = 0; t < 64; ++t)
+                v ^= ((zm >> t) & 1ull) ? src[t] : 0ull;
+        }
+        S.img[mp][i] = v;
+    }
+    __syncthreads();
+    for (int e = tid; e < NMAP * 8 * 16; e += NT) {
+        const int mp = e / 128, q = (e >> 4) & 7, vh = e & 15;
+        const u64 *im = S.img[mp] + 8 * q;
+        u64 base = 0;
+#pragma unroll
+        for (int bit = 0; bit < 4; ++bit)
+            base ^= ((vh >> bit) & 1) ? im[4 + bit] : 0ull;
+        gray16(base, im[0], im[1], im[2], im[3], S.tab[mp] + q * 256 + (vh << 4), 1);
+    }
+    __syncthreads();
+    const int g = blockIdx.x * NT + tid, gs = gridDim.x * NT;
+    for (int p = R0 + g; p < m; p += gs) {
+        if (p < R1) {
+            // pivot of panel b: its final words b and b + 1
+            const int t = p - R0;
+            if (out) {
+                out[(int64_t)p * ostride + b] = sb->newblk[t];
+                if (has1) {
+                    const u64 zt = sb->zpiv[t];
+                    u64 w1 = 0;
+                    for (int s2 = 0; s2 < kb; ++s2)
+                        w1 ^= ((zt >> s2) & 1ull) ? S.Ob1[s2] : 0ull;
+                    out[(int64_t)p * ostride + b + 1] = w1;
+                }
+            }
+            continue;
+        }
+        int ph;
+        if (p < R2) {
+            ph = sc->prow[p - R1];
+        } else if (sc) {
+            // panel c's order, else panel b's, else perm (panel b's positions read through sb)
+            ph = -1;
+            if (p < R1 + sc->nwin)
+                ph = sc->wperm[p - R1];
+            for (int x = 0; x < sc->nx && ph < 0; ++x)
+                if (sc->xpos[x] == p)
+                    ph = sc->xval[x];
+            if (ph < 0 && p < R0 + sb->nwin)
+                ph = sb->wperm[p - R0];
+            for (int x = 0; x < sb->nx && ph < 0; ++x)
+                if (sb->xpos[x] == p)
+                    ph = sb->xval[x];
+            if (ph < 0)
+                ph = perm[p];
+        } else {
+            ph = trailing_row(perm, sb, R0, sb->nwin, sb->nx, p);
+        }
+        uint64_t *row = A + (int64_t)ph * stride;
+        const u64 wb = row[b];
+        const u64 z1 = bytesum(S.tab[0], wb);
+        row[b] = bytesum(S.tab[1], wb);
+        zb[ph] = z1;
+        if (p < R2) {
+            if (out)
+                out[(int64_t)p * ostride + b + 1] = sc->newblk[p - R1];
+            continue;
+        }
+        if (sc) {
+            const u64 w1 = row[b + 1] ^ bytesum(S.tab[2], wb);
+            zc[ph] = bytesum(S.tab[3], w1);
+            row[b + 1] = bytesum(S.tab[4], w1);
+        }
+    }
+}
+
+constexpr size_t PAIR_SMEM = sizeof(PairSmem);
+constexpr size_t COORD_SMEM = sizeof(CoordSmem);
+
+}  // namespace
+
+namespace gf2 {
+
+int launch_pivot_pair(const Elim &e, int b, const u64 *side_prev, int64_t side_stride, const PanelState *st_prev,
+                      PanelState *st, bool defer, bool programmatic, cudaStream_t s);
+int init_states(const Elim &e, int nstates);
+
+static int sweep_pair(const Elim &e, int b, int wlo, int whi, bool paired, cudaStream_t s)
+{
+    static std::atomic<unsigned long long> attr_devs{0};
+    if (attr_needed(attr_devs)) {
+        cudaError_t err = cudaFuncSetAttribute(k_pair_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PAIR_SMEM);
+        if (err != cudaSuccess)
+            return note_cuda(err);
+        attr_done(attr_devs);
+    }
+    PairArgs a{};
+    a.A = e.A;
+    a.stride = e.stride;
+    a.perm = e.perm;
+    a.sb = e.st + (b & 3);
+    a.sc = e.st + ((b + 1) & 3);
+    a.zb = e.side;
+    a.zc = e.side + e.m;
+    a.out = e.out;
+    a.ostride = e.ostride;
+    a.m = (int)e.m;
+    a.W = (int)e.W;
+    a.b = b;
+    a.wlo = wlo;
+    a.whi = whi;
+    a.paired = paired ? 1 : 0;
+    const int nsm = sm_count();
+    // one SM left to the pivot search that runs meanwhile; an even count for pairs
+    int grid = e.grid > 0 ? e.grid : (nsm > 1 ? nsm - 1 : 1);
+    if (paired)
+        grid = grid >= 2 ? grid & ~1 : 2;
+    const int tok = prof_begin(s);
+    k_pair_sweep<<<grid, NT, PAIR_SMEM, s>>>(a);
+    prof_end(s, GF2_PROF_SWEEP, tok);
+    prof_launched(1);
+    return note_cuda(cudaGetLastError());
+}
+
+static int pair_coords(const Elim &e, int b, bool has_c, cudaStream_t s)
+{
+    static std::atomic<unsigned long long> attr_devs{0};
+    if (attr_needed(attr_devs)) {
+        cudaError_t err =
+            cudaFuncSetAttribute(k_pair_coords, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)COORD_SMEM);
+        if (err != cudaSuccess)
+            return note_cuda(err);
+        attr_done(attr_devs);
+    }
+    const int nsm = sm_count();
+    const int64_t need = (e.m + NT - 1) / NT;
+    const int grid = (int)(need < nsm ? (need > 0 ? need : 1) : nsm);
+    const int tok = prof_begin(s);
+    k_pair_coords<<<grid, NT, COORD_SMEM, s>>>(e.A, e.stride, e.perm, e.st + (b & 3), has_c ? e.st + ((b + 1) & 3) : nullptr,
+                                               e.side, e.side + e.m, e.out, e.ostride, (int)e.m, (int)e.W, b);
+    prof_end(s, GF2_PROF_COORDS, tok);
+    prof_launched(1);
+    return note_cuda(cudaGetLastError());
+}
+
+// Two panels per sweep (see the top of this file). Streams: pivot searches on e.s, the
+// coordinates and sweeps on aux.side. Panel b uses state slot b & 3: the pivot search of
+// panel b + 2 runs while the sweep of panels b, b + 1 still reads their slots.
+int elim_run_pair(const Elim &e, const ElimAux &aux)
+{
+    int rc;
+    if ((rc = init_states(e, 4)))
+        return rc;
+    const int W = (int)e.W;
+    if (W == 0)
+        return GF2_OK;
+    cudaStream_t s = e.s, t = aux.side;
+    cudaEvent_t ev_piv = aux.ev[0], ev_edge = aux.ev[1], ev_done = aux.ev[2];
+    for (int b = 0; b < W; b += 2) {
+        const bool has_c = b + 1 < W;
+        PanelState *sb = e.st + (b & 3), *sc = e.st + ((b + 1) & 3);
+        const PanelState *sp = e.st + ((b + 3) & 3);  // panel b - 1 (slot 3, initialised, for b = 0)
+        if (b >= 2 && (rc = note_cuda(cudaStreamWaitEvent(s, ev_edge, 0))))
+            return rc;
+        if ((rc = launch_pivot_pair(e, b, nullptr, 0, sp, sb, false, false, s)))
+            return rc;
+        if (has_c && (rc = launch_pivot_pair(e, b + 1, reinterpret_cast<const u64 *>(e.A) + b, e.stride, sb, sc, true, true, s)))
+            return rc;
+        if ((rc = note_cuda(cudaEventRecord(ev_piv, s))) || (rc = note_cuda(cudaStreamWaitEvent(t, ev_piv, 0))))
+            return rc;
+        if ((rc = pair_coords(e, b, has_c, t)))
+            return rc;
+        if (has_c && b + 2 < W) {
+            const int edge_end = b + 4 < W ? b + 4 : W;
+            if ((rc = sweep_pair(e, b, b + 2, edge_end, false, t)) || (rc = note_cuda(cudaEventRecord(ev_edge, t))))
+                return rc;
+            if (edge_end < W && (rc = sweep_pair(e, b, edge_end, W, true, t)))
+                return rc;
+        }
+    }
+    // the last panel's row order once every sweep and coordinate step is done
+    if ((rc = note_cuda(cudaEventRecord(ev_done, t))) || (rc = note_cuda(cudaStreamWaitEvent(s, ev_done, 0))))
+        return rc;
+    return apply_final_order(e);
+}
+
+}  // namespace gf2

@@ -30,7 +30,7 @@ constexpr int NSLOT = WIN / 32;
 // initialisation: identity row order, panel word 0 of every row, state reset
 // ---------------------------------------------------------------------------
 __global__ void k_init(const uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm,
-                       u64 *__restrict__ side0, PanelState *st, int m)
+                       u64 *__restrict__ side0, PanelState *st, int m, int nst = 2)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m) {
@@ -38,7 +38,7 @@ __global__ void k_init(const uint64_t *__restrict__ A, int64_t stride, int *__re
         if (side0)
             side0[i] = A[(int64_t)i * stride];
     }
-    if (i < 2 && st) {  // both panel states
+    if (i < nst && st) {  // every panel state slot
         st[i].nwin = 0;
         st[i].nx = 0;
         st[i].r_cur = 0;
@@ -118,6 +118,9 @@ struct PivotShared {
     // positions past the window swapped in this panel (position -> physical row)
     int nx;
     int xpos[64], xval[64];
+    // the previous panel's swaps past its window, while perm does not hold them yet
+    int pnx;
+    int pxpos[64], pxval[64];
 };
 
 // Context for the panel word b of a row: the previous panel's sweep updates
@@ -126,7 +129,8 @@ struct PivotShared {
 struct WordCtx {
     const uint64_t *A;
     int64_t stride;
-    const u64 *side_prev;  // panel word b - 1 of every row (nullptr for b = 0)
+    const u64 *side_prev;  // panel word b - 1 of every row (nullptr: A's word b is already current)
+    int64_t side_stride;   // words between consecutive rows of side_prev (1, or A's row pitch)
     int b;
 };
 
@@ -146,7 +150,7 @@ __device__ __forceinline__ u64 word_after(const PivotShared &S, u64 w, u64 v)
 __device__ __forceinline__ u64 panel_word(const WordCtx &c, const PivotShared &S, int ph)
 {
     const u64 w = c.A[(int64_t)ph * c.stride + c.b];
-    return c.side_prev ? word_after(S, w, c.side_prev[ph]) : w;
+    return c.side_prev ? word_after(S, w, c.side_prev[(int64_t)ph * c.side_stride]) : w;
 }
 
 // position -> physical row during the pivot search (perm plus this panel's swaps past the window)
@@ -155,6 +159,9 @@ __device__ __forceinline__ int perm_at(const int *__restrict__ perm, const Pivot
     for (int x = 0; x < S.nx; ++x)
         if (S.xpos[x] == p)
             return S.xval[x];
+    for (int x = 0; x < S.pnx; ++x)
+        if (S.pxpos[x] == p)
+            return S.pxval[x];
     return perm[p];
 }
 
@@ -585,13 +592,19 @@ static_assert(WIN <= PIVOT_THREADS, "one window row per thread when the window i
 // Pivot search of panel b. It first applies panel b - 1's row-order changes to
 // perm (no sweep reads those positions from perm), then forms the window: the
 // panel word b of the rows at positions r .. r + nwin - 1, from A plus panel
-// b - 1's contribution (side_prev = panel word b - 1 of every row; nullptr for
-// b = 0). This panel's own row-order changes go to st (nwin, wperm, nx, xpos,
-// xval) for the sweep of this panel and the pivot search of the next one.
+// b - 1's contribution (side_prev = panel word b - 1 of every row, side_stride
+// words apart; nullptr when A's word b already holds it, as for b = 0). This
+// panel's own row-order changes go to st (nwin, wperm, nx, xpos, xval) for the
+// sweep of this panel and the pivot search of the next one. st holds the state
+// of panel b - zt_lag on entry (the states rotate through zt_lag slots), whose
+// sweep has completed: the zero-tail test reads it. defer_prev: panel b - 1's
+// row order is left out of perm (a sweep still running reads those positions
+// there; the step after this search applies it) and taken from st_prev here.
 __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int64_t stride,
-                                            const u64 *__restrict__ side_prev, int *__restrict__ perm,
-                                            const PanelState *__restrict__ st_prev, PanelState *st, int64_t *P,
-                                            int64_t *Q, int m, int b, int nbits, int form, int thr_permille)
+                                            const u64 *__restrict__ side_prev, int64_t side_stride,
+                                            int *__restrict__ perm, const PanelState *__restrict__ st_prev,
+                                            PanelState *st, int64_t *P, int64_t *Q, int m, int b, int nbits,
+                                            int form, int thr_permille, int zt_lag = 2, bool defer_prev = false)
 {
     __shared__ PivotShared S;
     __shared__ u64 sXp[64], sXm[64];
@@ -602,9 +615,11 @@ __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int6
     // Zero tail: the sweep of panel b - 2 (complete: this search waits for it) found no
     // pivot and no nonzero word right of it in any trailing row, so no later panel has a
     // pivot. st still holds panel b - 2's state here (this search overwrites it below).
-    const int zt = st_prev->zero_tail || (b >= 2 && st->kbar == 0 && st->nz == 0 && st->r_next == r);
+    const int zt = st_prev->zero_tail || (b >= zt_lag && st->kbar == 0 && st->nz == 0 && st->r_next == r);
     const int nwin = (r < m && !zt) ? min(WIN, m - r) : 0;
-    const WordCtx wc{A, stride, b > 0 ? side_prev : nullptr, b};
+    // panel b - 1's contribution to word b is added here unless A holds it already
+    const bool contrib = b > 0 && side_prev != nullptr;
+    const WordCtx wc{A, stride, contrib ? side_prev : nullptr, side_stride, b};
     // window rows: the previous panel's order where it changed it, perm elsewhere
     // (one row per thread; nwin <= PIVOT_THREADS)
     int ph = 0;
@@ -624,23 +639,34 @@ __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int6
                     ph = perm[p];
             }
             w = A[(int64_t)ph * stride + b];
-            if (b > 0)
-                v = side_prev[ph];
+            if (contrib)
+                v = side_prev[(int64_t)ph * side_stride];
         }
         // apply the previous panel's order to perm (no sweep reads these positions from perm)
-        for (int i = tid; i < pn; i += PIVOT_THREADS)
-            perm[pr + i] = st_prev->wperm[i];
-        for (int x = tid; x < px; x += PIVOT_THREADS)
-            perm[st_prev->xpos[x]] = st_prev->xval[x];
+        if (!defer_prev) {
+            for (int i = tid; i < pn; i += PIVOT_THREADS)
+                perm[pr + i] = st_prev->wperm[i];
+            for (int x = tid; x < px; x += PIVOT_THREADS)
+                perm[st_prev->xpos[x]] = st_prev->xval[x];
+        }
+        // with the order deferred, the previous panel's window lies inside this one's (it
+        // starts at most 64 positions earlier and is no longer), so only its swaps past
+        // that window stay to be looked up
+        for (int x = tid; x < (defer_prev ? px : 0); x += PIVOT_THREADS) {
+            S.pxpos[x] = st_prev->xpos[x];
+            S.pxval[x] = st_prev->xval[x];
+        }
     }
-    if (b > 0 && tid < 64) {
+    if (contrib && tid < 64) {
         S.pZ[tid] = st_prev->zmap[tid];
         S.pO[tid] = tid < st_prev->kbar ? A[(int64_t)st_prev->prow[tid] * stride + b] : 0ull;
     }
-    if (tid == 0)
+    if (tid == 0) {
         S.nx = 0;
+        S.pnx = defer_prev && b > 0 ? st_prev->nx : 0;
+    }
     pivot_barrier();
-    if (b > 0)
+    if (contrib)
         for (int e = tid; e < 2 * 256; e += PIVOT_THREADS) {
             const int which = e >> 8, q = (e >> 4) & 15, vv = e & 15;
             const u64 *src = which ? S.pO : S.pZ;
@@ -653,7 +679,7 @@ __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int6
     pivot_barrier();
     if (tid < nwin) {
         S.Wph[tid] = ph;
-        S.Ww[tid] = b > 0 ? word_after(S, w, v) : w;
+        S.Ww[tid] = contrib ? word_after(S, w, v) : w;
     }
     pivot_barrier();
     if (warp == 0) {
@@ -821,7 +847,20 @@ k_pivot(const uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ 
 {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    pivot_panel(A, stride, side_prev, perm, st_prev, st, P, Q, m, b, nbits, form, thr_permille);
+    pivot_panel(A, stride, side_prev, 1, perm, st_prev, st, P, Q, m, b, nbits, form, thr_permille);
+}
+
+// Pivot search of one panel of a two-panel sweep step (gf2_pair.cu): states in four slots,
+// the previous panel's word from side_prev with any row pitch, its row order optionally
+// deferred. Programmatic dependent of the preceding search, as k_pivot.
+__global__ void __launch_bounds__(PIVOT_THREADS, 1)
+k_pivot_pair(const uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_prev, int64_t side_stride,
+             int *__restrict__ perm, const PanelState *__restrict__ st_prev, PanelState *st, int64_t *P, int64_t *Q,
+             int m, int b, int nbits, int defer)
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    pivot_panel(A, stride, side_prev, side_stride, perm, st_prev, st, P, Q, m, b, nbits, 0, 0, 4, defer != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -1344,7 +1383,7 @@ __global__ void __launch_bounds__(PIVOT_THREADS, 1) k_pivot_b(const gf2::ElimDes
 {
     const gf2::ElimDesc &d = D[idx[blockIdx.x]];
     const int nbits = min(64, d.n - 64 * b);
-    pivot_panel(d.A, d.stride, d.side + (size_t)((b + 1) & 1) * d.m, d.perm, d.st + ((b + 1) & 1), d.st + (b & 1),
+    pivot_panel(d.A, d.stride, d.side + (size_t)((b + 1) & 1) * d.m, 1, d.perm, d.st + ((b + 1) & 1), d.st + (b & 1),
                 d.P, d.Q, d.m, b, nbits, 0, 0);
 }
 
@@ -1496,7 +1535,7 @@ __device__ bool team_eliminate(SweepSmem &S, const gf2::ElimDesc &d, int tr, int
         return false;
     for (int b = 0; b < W; ++b) {
         if (tr == 0 && tid < PIVOT_THREADS)
-            pivot_panel(d.A, d.stride, d.side + (size_t)((b + 1) & 1) * m, d.perm, d.st + ((b + 1) & 1),
+            pivot_panel(d.A, d.stride, d.side + (size_t)((b + 1) & 1) * m, 1, d.perm, d.st + ((b + 1) & 1),
                         d.st + (b & 1), d.P, d.Q, m, b, min(64, d.n - 64 * b), 0, 0);
         if (!team_barrier(bar, target, G, pl))
             return false;
@@ -1776,8 +1815,47 @@ int elim_run(const Elim &e)
     return elim_run(e, aux);
 }
 
+int launch_pivot_pair(const Elim &e, int b, const u64 *side_prev, int64_t side_stride, const PanelState *st_prev,
+                      PanelState *st, bool defer, bool programmatic, cudaStream_t s)
+{
+    const int nbits = (int)((e.n - 64ll * b) < 64 ? (e.n - 64ll * b) : 64);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(PIVOT_THREADS);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = programmatic ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int tok = prof_begin(s);
+    int rc = note_cuda(cudaLaunchKernelEx(&cfg, k_pivot_pair, (const uint64_t *)e.A, e.stride, side_prev, side_stride,
+                                          e.perm, st_prev, st, e.P, e.Q, (int)e.m, b, nbits, defer ? 1 : 0));
+    prof_end(s, GF2_PROF_PIVOT, tok);
+    prof_launched(1);
+    return rc ? rc : note_cuda(cudaGetLastError());
+}
+
+int init_states(const Elim &e, int nstates)
+{
+    const int m = (int)e.m;
+    k_init<<<(m + 255) / 256 > 0 ? (m + 255) / 256 : 1, 256, 0, e.s>>>(e.A, e.stride, e.perm, nullptr, e.st, m,
+                                                                       nstates);
+    prof_launched(1);
+    return note_cuda(cudaGetLastError());
+}
+
+int apply_final_order(const Elim &e)
+{
+    k_apply_order<<<1, 128, 0, e.s>>>(e.perm, e.stf);
+    prof_launched(1);
+    return note_cuda(cudaGetLastError());
+}
+
 int elim_run(const Elim &e, const ElimAux &aux)
 {
+    if (e.pps == 2 && e.mode == 0)
+        return elim_run_pair(e, aux);
     const int m = (int)e.m;
     k_init<<<(m + 255) / 256, 256, 0, e.s>>>(e.A, e.stride, e.perm, e.side, e.st, m);
     prof_launched(1);

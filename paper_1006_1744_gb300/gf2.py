@@ -43,7 +43,7 @@ class Gf2Error(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("k", _int), ("tile_words", _int), ("grid_ctas", _int), ("product", _int),
                 ("cutoff_cols", _i64), ("rref_method", _int), ("hybrid_permille", _int), ("batch_mode", _int),
-                ("reserved", _int * 5)]
+                ("panels_per_sweep", _int), ("reserved", _int * 4)]
 
 
 class BatchItem(ctypes.Structure):
@@ -75,7 +75,7 @@ SYMBOLS = {
     "gf2_prof_collect": (_int, [_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
 }
 
-PROF_SWEEP, PROF_PIVOT, PROF_RREF, PROF_MUL = 0, 1, 2, 3
+PROF_SWEEP, PROF_PIVOT, PROF_RREF, PROF_MUL, PROF_COORDS = 0, 1, 2, 3, 4
 
 
 def replay_enable(on: bool) -> None:
