@@ -10,20 +10,22 @@
 //     then of panel c = b + 1 (A's word b + 1 plus panel b's contribution, the
 //     look-ahead of the one-panel pipeline), panel b's row order left out of
 //     perm while the previous sweep still reads it;
-//   * k_pair_coords: the coordinates z_b of every row below panel b's pivots over
+//   * k_pair_front: the coordinates z_b of every row below panel b's pivots over
 //     panel b's pivot rows O_b, and z_c of every row below both panels' pivots
 //     over O_c (panel c's pivot rows after panel b), from its words b and b + 1;
-//     it writes the multipliers of L into words b and b + 1, the pivot rows'
-//     final words b and b + 1 into `out`, and panel b's row order into perm;
+//     it writes the multipliers of L into words b and b + 1, both panels'
+//     updates into words b + 2 and b + 3 (the next pair's panel words), the
+//     pivot rows' final words b .. b + 3 into `out`, and panel b's row order into
+//     perm. Byte tables of the linear maps involved do all of it;
 //   * k_pair_sweep: MakeTable1 for both panels on 8-word column tiles, O_c formed
 //     from O_b's tables, and row ^= z_b.O_b ^ z_c.O_c on every trailing row from
-//     word b + 2 on. One 128-byte line of shared memory holds entry v of both
+//     word b + 4 on. One 128-byte line of shared memory holds entry v of both
 //     panels' tables; the two rows of a quarter-warp read opposite halves of
 //     their lines, so every lookup instruction is free of bank conflicts. The two
 //     CTAs of a pair take the two halves of the same 128-byte lines of the same
 //     rows, so each line is fetched from DRAM once.
-// A pair's sweep is two launches: words b + 2 and b + 3 first (all the next
-// pair's pivot searches read), then the rest, during which those searches run.
+// The next pair's pivot searches need only words b + 2 and b + 3, so they run
+// while the sweep of the rest goes on.
 // Every result equals the one-panel pipeline's, hence the Gaussian PLS's.
 #include <climits>
 
@@ -333,18 +335,26 @@ __global__ void __launch_bounds__(NT, 1) k_pair_sweep(PairArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Coordinates of the rows of a pair, and the multipliers of L in its two panel words.
-// Byte tables (8 byte positions x 256 values) of five linear maps of a panel word:
-//   Zb: word b -> z_b (panel b's zmap), Xb: word b -> panel b's multipliers (z_b.X_b, X_t =
-//   pivot t's multipliers plus its own bit), Cb: word b -> panel b's contribution to word b + 1
-//   (z_b.O_b[b + 1]), and likewise Zc, Xc for panel c from word b + 1 after panel b.
+// The front of a pair: every row's coordinates, the multipliers of L in words b and b + 1, and
+// both panels' updates of words b + 2 and b + 3 (the next pair's panel words), all from byte
+// tables (8 byte positions x 256 values) of linear maps of a row's panel words:
+//   from word b:                   Zb -> z_b, Xb -> panel b's multipliers (z_b.X_b, X_t = pivot
+//                                  t's multipliers plus its own bit), Cb, E2b, E3b -> z_b.O_b at
+//                                  words b + 1, b + 2, b + 3;
+//   from word b + 1 after panel b: Zc -> z_c, Xc -> panel c's multipliers, E2c, E3c -> z_c.O_c at
+//                                  words b + 2, b + 3.
 // ---------------------------------------------------------------------------
-constexpr int NMAP = 5;
+constexpr int NMAP = 9;
+enum { M_ZB, M_XB, M_CB, M_E2B, M_E3B, M_ZC, M_XC, M_E2C, M_E3C };
 
-struct CoordSmem {
+struct FrontSmem {
     u64 tab[NMAP][8 * 256];
     u64 img[NMAP][64];   // image of each bit of the panel word
-    u64 Xb[64], Xc[64], Ob1[64];
+    u64 Xb[64], Xc[64];
+    u64 Ob[3][64];       // panel b's pivot rows at words b + 1, b + 2, b + 3
+    u64 Oc[3][64];       // panel c's pivot rows: word b (raw), then words b + 2, b + 3 after panel b
+    u64 zmb[64], zmc[64];  // the panels' zmaps
+    int sc_[6];          // r_cur, kbar of panel b, kbar of panel c, window and swaps of b and c
 };
 
 __device__ __forceinline__ u64 bytesum(const u64 *__restrict__ t, u64 w)
@@ -356,117 +366,208 @@ __device__ __forceinline__ u64 bytesum(const u64 *__restrict__ t, u64 w)
     return a;
 }
 
+// sum of src[s] over the set bits s of z (64 independent loads, four XOR chains)
+__device__ __forceinline__ u64 select_sum(u64 z, const u64 *__restrict__ src)
+{
+    u64 a[4] = {0ull, 0ull, 0ull, 0ull};
+#pragma unroll
+    for (int s2 = 0; s2 < 64; ++s2)
+        a[s2 & 3] ^= ((z >> s2) & 1ull) ? src[s2] : 0ull;
+    return (a[0] ^ a[1]) ^ (a[2] ^ a[3]);
+}
+
+// Physical row at trailing position p >= R2 of a pair: panel c's order, else panel b's, else perm
+// (the positions panel b changed are read through sb: this kernel writes them into perm).
+__device__ __forceinline__ int pair_row(const int *__restrict__ perm, const PanelState *__restrict__ sb,
+                                        const PanelState *__restrict__ sc, int R0, int R1, int nwb, int nxb, int nwc,
+                                        int nxc, int p)
+{
+    if (sc) {
+        if (p < R1 + nwc)
+            return sc->wperm[p - R1];
+        for (int x = 0; x < nxc; ++x)
+            if (sc->xpos[x] == p)
+                return sc->xval[x];
+    }
+    if (p < R0 + nwb)
+        return sb->wperm[p - R0];
+    for (int x = 0; x < nxb; ++x)
+        if (sb->xpos[x] == p)
+            return sb->xval[x];
+    return perm[p];
+}
+
 __global__ void __launch_bounds__(NT, 1)
-k_pair_coords(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, const PanelState *__restrict__ sb,
-              const PanelState *__restrict__ sc, u64 *__restrict__ zb, u64 *__restrict__ zc,
-              uint64_t *__restrict__ out, int64_t ostride, int m, int W, int b)
+k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, const PanelState *__restrict__ sb,
+             const PanelState *__restrict__ sc, u64 *__restrict__ zb, u64 *__restrict__ zc,
+             uint64_t *__restrict__ out, int64_t ostride, int m, int W, int b)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    CoordSmem &S = *reinterpret_cast<CoordSmem *>(smraw);
+    FrontSmem &S = *reinterpret_cast<FrontSmem *>(smraw);
     const int tid = threadIdx.x;
-    const int kb = sb->kbar, kc = sc ? sc->kbar : 0;
-    const int R0 = sb->r_cur, R1 = R0 + kb, R2 = R1 + kc;
-    const bool has1 = b + 1 < W;  // word b + 1 exists
-    // panel b's row order into perm (its pivot search of panel c left it out): only positions
-    // that this kernel reads through sb, never through perm
+    if (tid < 6)
+        S.sc_[tid] = tid == 0 ? sb->r_cur : tid == 1 ? sb->kbar : tid == 2 ? (sc ? sc->kbar : 0)
+                   : tid == 3 ? sb->nwin : tid == 4 ? sb->nx : (sc ? sc->nwin * 256 + sc->nx : 0);
+    if (tid >= 64 && tid < 128)
+        S.zmb[tid - 64] = sb->zmap[tid - 64];
+    if (tid >= 128 && tid < 192)
+        S.zmc[tid - 128] = sc ? sc->zmap[tid - 128] : 0ull;
+    __syncthreads();
+    const int kb = S.sc_[1], kc = S.sc_[2];
+    const int R0 = S.sc_[0], R1 = R0 + kb, R2 = R1 + kc;
+    const int nwb = S.sc_[3], nxb = S.sc_[4], nwc = S.sc_[5] >> 8, nxc = S.sc_[5] & 255;
+    const bool has1 = b + 1 < W, has2 = b + 2 < W, has3 = b + 3 < W;
+    const int g = blockIdx.x * NT + tid, gs = gridDim.x * NT;
+    // panel b's row order into perm (its pivot search of panel c left it out)
     if (sc) {
-        const int g = blockIdx.x * NT + tid, gs = gridDim.x * NT;
-        for (int i = g; i < sb->nwin; i += gs)
+        for (int i = g; i < nwb; i += gs)
             perm[R0 + i] = sb->wperm[i];
-        for (int x = g; x < sb->nx; x += gs)
+        for (int x = g; x < nxb; x += gs)
             perm[sb->xpos[x]] = sb->xval[x];
     }
-    if (kb == 0 && kc == 0)
-        return;  // words b and b + 1 of every row below are zero already
+    if ((kb == 0 && kc == 0) || R0 + blockIdx.x * NT >= m)
+        return;  // no pivot: the words below are zero at b, b + 1 and unchanged right of them
+    // this thread's first row: its words are loaded while the tables are built
+    int p = R0 + g, ph = -1;
+    u64 w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+    if (p >= R1 && p < m) {
+        ph = p < R2 ? sc->prow[p - R1] : pair_row(perm, sb, sc, R0, R1, nwb, nxb, nwc, nxc, p);
+        const uint64_t *row = A + (int64_t)ph * stride + b;
+        w0 = row[0];
+        if (p >= R2) {
+            w1 = has1 ? row[1] : 0ull;
+            w2 = has2 ? row[2] : 0ull;
+            w3 = has3 ? row[3] : 0ull;
+        }
+    }
     if (tid < 64) {
         const int t = tid;
+        const uint64_t *rb = A + (int64_t)(t < kb ? sb->prow[t] : 0) * stride + b;
+        const uint64_t *rc = A + (int64_t)(t < kc ? sc->prow[t] : 0) * stride + b;
         S.Xb[t] = t < kb ? sb->newblk[t] & sb->J & lowmask(sb->pcol[t] + 1) : 0ull;
-        S.Ob1[t] = t < kb && has1 ? A[(int64_t)sb->prow[t] * stride + b + 1] : 0ull;
+        S.Ob[0][t] = t < kb && has1 ? rb[1] : 0ull;
+        S.Ob[1][t] = t < kb && has2 ? rb[2] : 0ull;
+        S.Ob[2][t] = t < kb && has3 ? rb[3] : 0ull;
         S.Xc[t] = t < kc ? sc->newblk[t] & sc->J & lowmask(sc->pcol[t] + 1) : 0ull;
+        S.Oc[0][t] = t < kc ? rc[0] : 0ull;
+        S.Oc[1][t] = t < kc && has2 ? rc[2] : 0ull;
+        S.Oc[2][t] = t < kc && has3 ? rc[3] : 0ull;
     }
     __syncthreads();
-    if (tid < NMAP * 64) {
+    if (tid < 5 * 64) {
+        // panel b's maps: bit i of word b -> ...
         const int mp = tid >> 6, i = tid & 63;
-        const u64 zm = mp < 3 ? sb->zmap[i] : (sc ? sc->zmap[i] : 0ull);
-        u64 v = 0;
-        if (mp == 0 || mp == 3) {
-            v = zm;
-        } else {
-            const u64 *src = mp == 1 ? S.Xb : mp == 2 ? S.Ob1 : S.Xc;
-            for (int t = 0; t < 64; ++t)
-                v ^= ((zm >> t) & 1ull) ? src[t] : 0ull;
+        const u64 zm = S.zmb[i];
+        const u64 *src = mp == 1 ? S.Xb : mp == 2 ? S.Ob[0] : mp == 3 ? S.Ob[1] : S.Ob[2];
+        S.img[mp][i] = mp == 0 ? zm : select_sum(zm, src);
+    } else if (tid < 5 * 64 + 64) {
+        // panel c's pivot rows at words b + 2, b + 3 after panel b (their coordinates over O_b
+        // from their word b)
+        const int t = tid - 5 * 64;
+        if (t < kc) {
+            const u64 zt = select_sum(S.Oc[0][t], S.zmb);
+            S.Oc[1][t] ^= select_sum(zt, S.Ob[1]);
+            S.Oc[2][t] ^= select_sum(zt, S.Ob[2]);
         }
-        S.img[mp][i] = v;
     }
     __syncthreads();
-    for (int e = tid; e < NMAP * 8 * 16; e += NT) {
-        const int mp = e / 128, q = (e >> 4) & 7, vh = e & 15;
-        const u64 *im = S.img[mp] + 8 * q;
-        u64 base = 0;
+    if (tid < 4 * 64) {
+        const int mp = tid >> 6, i = tid & 63;
+        const u64 zm = S.zmc[i];
+        const u64 *src = mp == 1 ? S.Xc : mp == 2 ? S.Oc[1] : S.Oc[2];
+        S.img[M_ZC + mp][i] = mp == 0 ? zm : select_sum(zm, src);
+    }
+    __syncthreads();
+    {
+        // a warp per (map, byte position): lane l writes entries l + 32 k, whose low nibble
+        // (l & 15) is fixed and whose high nibble is (l >> 4) + 2 k: consecutive lanes store
+        // consecutive entries (no bank conflict)
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int pq = warp; pq < NMAP * 8; pq += NT / 32) {
+            const int mp = pq >> 3, q = pq & 7;
+            const u64 *im = S.img[mp] + 8 * q;
+            u64 lo = 0;
 #pragma unroll
-        for (int bit = 0; bit < 4; ++bit)
-            base ^= ((vh >> bit) & 1) ? im[4 + bit] : 0ull;
-        gray16(base, im[0], im[1], im[2], im[3], S.tab[mp] + q * 256 + (vh << 4), 1);
+            for (int bit = 0; bit < 4; ++bit)
+                lo ^= ((lane >> bit) & 1) ? im[bit] : 0ull;
+            u64 *dst = S.tab[mp] + q * 256 + lane;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int hn = (lane >> 4) + 2 * k;
+                u64 hi = 0;
+#pragma unroll
+                for (int bit = 0; bit < 4; ++bit)
+                    hi ^= ((hn >> bit) & 1) ? im[4 + bit] : 0ull;
+                dst[32 * k] = lo ^ hi;
+            }
+        }
     }
     __syncthreads();
-    const int g = blockIdx.x * NT + tid, gs = gridDim.x * NT;
-    for (int p = R0 + g; p < m; p += gs) {
+    for (; p < m; p += gs) {
+        if (ph < 0 && p >= R1) {
+            // a later row of this thread (more rows than threads)
+            ph = p < R2 ? sc->prow[p - R1] : pair_row(perm, sb, sc, R0, R1, nwb, nxb, nwc, nxc, p);
+            const uint64_t *row = A + (int64_t)ph * stride + b;
+            w0 = row[0];
+            if (p >= R2) {
+                w1 = has1 ? row[1] : 0ull;
+                w2 = has2 ? row[2] : 0ull;
+                w3 = has3 ? row[3] : 0ull;
+            }
+        }
         if (p < R1) {
-            // pivot of panel b: its final words b and b + 1
+            // pivot of panel b: its final words b .. b + 3
             const int t = p - R0;
             if (out) {
-                out[(int64_t)p * ostride + b] = sb->newblk[t];
-                if (has1) {
-                    const u64 zt = sb->zpiv[t];
-                    u64 w1 = 0;
-                    for (int s2 = 0; s2 < kb; ++s2)
-                        w1 ^= ((zt >> s2) & 1ull) ? S.Ob1[s2] : 0ull;
-                    out[(int64_t)p * ostride + b + 1] = w1;
-                }
+                uint64_t *o = out + (int64_t)p * ostride + b;
+                const u64 zt = sb->zpiv[t];
+                o[0] = sb->newblk[t];
+                if (has1)
+                    o[1] = select_sum(zt, S.Ob[0]);
+                if (has2)
+                    o[2] = select_sum(zt, S.Ob[1]);
+                if (has3)
+                    o[3] = select_sum(zt, S.Ob[2]);
             }
-            continue;
-        }
-        int ph;
-        if (p < R2) {
-            ph = sc->prow[p - R1];
-        } else if (sc) {
-            // panel c's order, else panel b's, else perm (panel b's positions read through sb)
-            ph = -1;
-            if (p < R1 + sc->nwin)
-                ph = sc->wperm[p - R1];
-            for (int x = 0; x < sc->nx && ph < 0; ++x)
-                if (sc->xpos[x] == p)
-                    ph = sc->xval[x];
-            if (ph < 0 && p < R0 + sb->nwin)
-                ph = sb->wperm[p - R0];
-            for (int x = 0; x < sb->nx && ph < 0; ++x)
-                if (sb->xpos[x] == p)
-                    ph = sb->xval[x];
-            if (ph < 0)
-                ph = perm[p];
+        } else if (p < R2) {
+            // pivot of panel c: panel b's multipliers in A, its final words b + 1 .. b + 3
+            const int t = p - R1;
+            uint64_t *row = A + (int64_t)ph * stride + b;
+            zb[ph] = bytesum(S.tab[M_ZB], w0);
+            row[0] = bytesum(S.tab[M_XB], w0);
+            if (out) {
+                uint64_t *o = out + (int64_t)p * ostride + b;
+                const u64 zt = sc->zpiv[t];
+                o[1] = sc->newblk[t];
+                if (has2)
+                    o[2] = select_sum(zt, S.Oc[1]);
+                if (has3)
+                    o[3] = select_sum(zt, S.Oc[2]);
+            }
         } else {
-            ph = trailing_row(perm, sb, R0, sb->nwin, sb->nx, p);
+            uint64_t *row = A + (int64_t)ph * stride + b;
+            const u64 zbv = bytesum(S.tab[M_ZB], w0);
+            u64 n2 = w2 ^ bytesum(S.tab[M_E2B], w0), n3 = w3 ^ bytesum(S.tab[M_E3B], w0);
+            row[0] = bytesum(S.tab[M_XB], w0);
+            zb[ph] = zbv;
+            if (sc) {
+                const u64 v1 = w1 ^ bytesum(S.tab[M_CB], w0);
+                zc[ph] = bytesum(S.tab[M_ZC], v1);
+                row[1] = bytesum(S.tab[M_XC], v1);
+                n2 ^= bytesum(S.tab[M_E2C], v1);
+                n3 ^= bytesum(S.tab[M_E3C], v1);
+            }
+            if (has2)
+                row[2] = n2;
+            if (has3)
+                row[3] = n3;
         }
-        uint64_t *row = A + (int64_t)ph * stride;
-        const u64 wb = row[b];
-        const u64 z1 = bytesum(S.tab[0], wb);
-        row[b] = bytesum(S.tab[1], wb);
-        zb[ph] = z1;
-        if (p < R2) {
-            if (out)
-                out[(int64_t)p * ostride + b + 1] = sc->newblk[p - R1];
-            continue;
-        }
-        if (sc) {
-            const u64 w1 = row[b + 1] ^ bytesum(S.tab[2], wb);
-            zc[ph] = bytesum(S.tab[3], w1);
-            row[b + 1] = bytesum(S.tab[4], w1);
-        }
+        ph = -1;
     }
 }
 
 constexpr size_t PAIR_SMEM = sizeof(PairSmem);
-constexpr size_t COORD_SMEM = sizeof(CoordSmem);
+constexpr size_t FRONT_SMEM = sizeof(FrontSmem);
 
 }  // namespace
 
@@ -513,12 +614,12 @@ static int sweep_pair(const Elim &e, int b, int wlo, int whi, bool paired, cudaS
     return note_cuda(cudaGetLastError());
 }
 
-static int pair_coords(const Elim &e, int b, bool has_c, cudaStream_t s)
+static int pair_front(const Elim &e, int b, bool has_c, cudaStream_t s)
 {
     static std::atomic<unsigned long long> attr_devs{0};
     if (attr_needed(attr_devs)) {
         cudaError_t err =
-            cudaFuncSetAttribute(k_pair_coords, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)COORD_SMEM);
+            cudaFuncSetAttribute(k_pair_front, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FRONT_SMEM);
         if (err != cudaSuccess)
             return note_cuda(err);
         attr_done(attr_devs);
@@ -527,8 +628,8 @@ static int pair_coords(const Elim &e, int b, bool has_c, cudaStream_t s)
     const int64_t need = (e.m + NT - 1) / NT;
     const int grid = (int)(need < nsm ? (need > 0 ? need : 1) : nsm);
     const int tok = prof_begin(s);
-    k_pair_coords<<<grid, NT, COORD_SMEM, s>>>(e.A, e.stride, e.perm, e.st + (b & 3), has_c ? e.st + ((b + 1) & 3) : nullptr,
-                                               e.side, e.side + e.m, e.out, e.ostride, (int)e.m, (int)e.W, b);
+    k_pair_front<<<grid, NT, FRONT_SMEM, s>>>(e.A, e.stride, e.perm, e.st + (b & 3), has_c ? e.st + ((b + 1) & 3) : nullptr,
+                                              e.side, e.side + e.m, e.out, e.ostride, (int)e.m, (int)e.W, b);
     prof_end(s, GF2_PROF_COORDS, tok);
     prof_launched(1);
     return note_cuda(cudaGetLastError());
@@ -559,15 +660,12 @@ int elim_run_pair(const Elim &e, const ElimAux &aux)
             return rc;
         if ((rc = note_cuda(cudaEventRecord(ev_piv, s))) || (rc = note_cuda(cudaStreamWaitEvent(t, ev_piv, 0))))
             return rc;
-        if ((rc = pair_coords(e, b, has_c, t)))
+        // the front: coordinates, multipliers, words b + 2 and b + 3 (what the next pair's
+        // pivot searches read), then the rest of the trailing block
+        if ((rc = pair_front(e, b, has_c, t)) || (rc = note_cuda(cudaEventRecord(ev_edge, t))))
             return rc;
-        if (has_c && b + 2 < W) {
-            const int edge_end = b + 4 < W ? b + 4 : W;
-            if ((rc = sweep_pair(e, b, b + 2, edge_end, false, t)) || (rc = note_cuda(cudaEventRecord(ev_edge, t))))
-                return rc;
-            if (edge_end < W && (rc = sweep_pair(e, b, edge_end, W, true, t)))
-                return rc;
-        }
+        if (has_c && b + 4 < W && (rc = sweep_pair(e, b, b + 4, W, true, t)))
+            return rc;
     }
     // the last panel's row order once every sweep and coordinate step is done
     if ((rc = note_cuda(cudaEventRecord(ev_done, t))) || (rc = note_cuda(cudaStreamWaitEvent(s, ev_done, 0))))
