@@ -649,8 +649,8 @@ def run_headline(args):
     synth_gpu.fill(A0, n, SEED + rank)
     A1 = torch.empty_like(A0)
     A2 = torch.empty_like(A0) if with_rref else None
-    wp = gf2.new_workspace(gf2.OP_PLS, m, n, device=dev)
-    wr = gf2.new_workspace(gf2.OP_RREF, m, n, device=dev) if with_rref else None
+    wp = gf2.new_workspace(gf2.OP_PLS, m, n, device=dev, opts=opts)
+    wr = gf2.new_workspace(gf2.OP_RREF, m, n, device=dev, opts=opts) if with_rref else None
     P = torch.empty(m, dtype=torch.int64, device=dev)
     Q = torch.empty(n, dtype=torch.int64, device=dev)
     r1 = torch.empty(1, dtype=torch.int64, device=dev)

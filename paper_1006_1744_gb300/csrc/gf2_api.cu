@@ -36,7 +36,22 @@ int64_t min_stride(int64_t n)
     return s < 16 ? 16 : s;
 }
 
-ElimLayout elim_layout(int op, int64_t m, int64_t n)
+int pps_choice(const gf2_opts *o, int64_t m, int64_t n)
+{
+    if (o && o->panels_per_sweep)
+        return o->panels_per_sweep;
+    return 1;
+}
+
+// gf2_rref: the PLS route takes the panels per sweep of the PLS form; the reduced-form routes
+// sweep one panel at a time
+static int rref_pps(const gf2_opts *o, int64_t m, int64_t n)
+{
+    const int method = (o && o->rref_method) ? o->rref_method : GF2_RREF_PLS;
+    return method == GF2_RREF_PLS ? pps_choice(o, m, n) : 1;
+}
+
+ElimLayout elim_layout(int op, int64_t m, int64_t n, int pps)
 {
     ElimLayout L{};
     const int64_t W = (n + 63) / 64;
@@ -47,7 +62,9 @@ ElimLayout elim_layout(int op, int64_t m, int64_t n)
     L.perm = off;
     off = align_up(off + (size_t)m * sizeof(int), 256);
     L.side = off;
-    off = align_up(off + (size_t)2 * m * sizeof(u64), 256);
+    // two panel words of every row (double buffered); two panels per sweep: the coordinates of
+    // every row over both panels' pivot rows, and words b .. b + 3 of every row (double buffered)
+    off = align_up(off + (size_t)(pps == 2 ? 10 : 2) * m * sizeof(u64), 256);
     L.pmask = off;
     off = align_up(off + (size_t)(W + 1) * sizeof(u64), 256);
     L.out = off;
@@ -170,7 +187,7 @@ int check_opts(const gf2_opts *o)
 }
 
 static Elim make_elim(uint64_t *A, int64_t m, int64_t n, int64_t stride, char *work, const ElimLayout &L,
-                      int64_t *P, int64_t *Q, bool with_out, const gf2_opts *o, cudaStream_t s)
+                      int64_t *P, int64_t *Q, bool with_out, const gf2_opts *o, cudaStream_t s, int pps = 1)
 {
     Elim e{};
     e.A = A;
@@ -193,7 +210,7 @@ static Elim make_elim(uint64_t *A, int64_t m, int64_t n, int64_t stride, char *w
     e.mode = 0;
     e.hybrid_permille = o ? o->hybrid_permille : 0;
     e.k = (o && o->k) ? o->k : 8;
-    e.pps = (o && o->panels_per_sweep) ? o->panels_per_sweep : 1;
+    e.pps = pps;
     if (e.pps == 2)
         e.stf = e.W > 0 ? e.st + ((e.W - 1) & 3) : e.st;  // panel b's state lives in slot b & 3
     // default: one CTA per SM but one, so the look-ahead pivot search (which cannot share an
@@ -273,10 +290,11 @@ size_t gf2_workspace_bytes(int op, int64_t m, int64_t n, const gf2_opts *opts)
     case GF2_OP_PLS:
         if (opts && opts->cutoff_cols > 0 && n > opts->cutoff_cols)
             return rec_workspace_bytes(m, n, opts->cutoff_cols);
-        return elim_layout(op, m, n).total;
+        return elim_layout(op, m, n, pps_choice(opts, m, n)).total;
     case GF2_OP_RREF:
+        return elim_layout(op, m, n, rref_pps(opts, m, n)).total;
     case GF2_OP_RANK:
-        return elim_layout(op, m, n).total;
+        return elim_layout(op, m, n, pps_choice(opts, m, n)).total;
     case GF2_OP_MUL:  // (m, n) = (inner dimension k, columns n); Strassen forms: a k x k A assumed
         if (opts && (opts->product == GF2_PRODUCT_STRASSEN || opts->product == GF2_PRODUCT_STRASSEN_TENSOR))
             return gf2_mul_workspace_bytes(m, m, n, opts);
@@ -305,10 +323,11 @@ int gf2_pls(uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *P, int64
             return rc;
         return pls_recursive(A, stride, m, n, P, Q, rank, (char *)work, opts, s);
     }
-    const ElimLayout L = elim_layout(GF2_OP_PLS, m, n);
+    const int pps = pps_choice(opts, m, n);
+    const ElimLayout L = elim_layout(GF2_OP_PLS, m, n, pps);
     if ((rc = get_work(work, work_bytes, L.total)))
         return rc;
-    const Elim e = make_elim(A, m, n, stride, (char *)work, L, P, Q, true, opts, s);
+    const Elim e = make_elim(A, m, n, stride, (char *)work, L, P, Q, true, opts, s, pps);
     return run_replayed(call_key(GF2_OP_PLS, A, m, n, stride, P, Q, rank, nullptr, work, work_bytes, e), s,
                         [&](cudaStream_t st) {
                             Elim es = e;
@@ -333,22 +352,19 @@ int gf2_rref(uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *rank, i
     cudaStream_t s = (cudaStream_t)stream;
     if (m == 0 || n == 0)
         return identity_fill(nullptr, 0, pivots, pivots ? n : 0, rank, s);
-    const ElimLayout L = elim_layout(GF2_OP_RREF, m, n);
+    const int pps = rref_pps(opts, m, n);
+    const ElimLayout L = elim_layout(GF2_OP_RREF, m, n, pps);
     if ((rc = get_work(work, work_bytes, L.total)))
         return rc;
     char *w = (char *)work;
     int64_t *Qs = reinterpret_cast<int64_t *>(w + q_scratch_offset(L, n));
-    Elim e = make_elim(A, m, n, stride, w, L, nullptr, Qs, true, opts, s);
+    Elim e = make_elim(A, m, n, stride, w, L, nullptr, Qs, true, opts, s, pps);
     const int method = (opts && opts->rref_method) ? opts->rref_method : GF2_RREF_PLS;
     // the sweep form: PLS panels (then the upper solve), reduced-form panels (M4RI), or the hybrid
     e.mode = method == GF2_RREF_M4RI ? 1 : method == GF2_RREF_HYBRID ? 2 : 0;
     e.ups = reinterpret_cast<u64 *>(w + L.ups);
     if (e.mode && e.tile_words != 16)
         return GF2_EINVAL;  // the reduced form is built on the 16-word sweep only
-    if (e.mode && e.pps != 1) {
-        e.pps = 1;  // the reduced form sweeps one panel at a time
-        e.stf = final_state(e.st, e.W);
-    }
     CallKey key = call_key(GF2_OP_RREF + 16 * e.mode, A, m, n, stride, nullptr, nullptr, rank, pivots, work,
                            work_bytes, e);
     key.grid += e.hybrid_permille << 16;  // the threshold changes the launches' behaviour
@@ -375,13 +391,14 @@ int gf2_rank(const uint64_t *A, int64_t m, int64_t n, int64_t stride, int64_t *r
     cudaStream_t s = (cudaStream_t)stream;
     if (m == 0 || n == 0)
         return identity_fill(nullptr, 0, nullptr, 0, rank, s);
-    const ElimLayout L = elim_layout(GF2_OP_RANK, m, n);
+    const int pps = pps_choice(opts, m, n);
+    const ElimLayout L = elim_layout(GF2_OP_RANK, m, n, pps);
     if ((rc = get_work(work, work_bytes, L.total)))
         return rc;
     char *w = (char *)work;
     uint64_t *copy = reinterpret_cast<uint64_t *>(w + L.out);
     const int64_t cs = min_stride(n);
-    const Elim e = make_elim(copy, m, n, cs, w, L, nullptr, nullptr, false, opts, s);
+    const Elim e = make_elim(copy, m, n, cs, w, L, nullptr, nullptr, false, opts, s, pps);
     return run_replayed(call_key(GF2_OP_RANK, A, m, n, stride, nullptr, nullptr, rank, nullptr, work, work_bytes, e),
                         s, [&](cudaStream_t st) {
                             cudaError_t err = cudaMemcpy2DAsync(copy, (size_t)cs * 8, A, (size_t)stride * 8,

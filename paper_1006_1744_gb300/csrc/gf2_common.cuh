@@ -243,7 +243,8 @@ struct ElimLayout {
     size_t total;
 };
 int64_t min_stride(int64_t n);
-ElimLayout elim_layout(int op, int64_t m, int64_t n);
+ElimLayout elim_layout(int op, int64_t m, int64_t n, int pps = 1);  // pps: panels per sweep (1 or 2)
+int pps_choice(const gf2_opts *o, int64_t m, int64_t n);           // panels per sweep of a PLS-form elimination
 
 // The state a finished elimination leaves its rank in: the one of its last panel.
 __host__ __device__ inline PanelState *final_state(PanelState *st, int64_t W) { return st + ((W + 1) & 1); }

@@ -52,6 +52,7 @@ struct PairArgs {
     const int *perm;
     const PanelState *sb, *sc;
     const u64 *zb, *zc;  // per physical row: coordinates over O_b, over O_c
+    u64 *F;              // next pair's panel words: words b + 4, b + 5 of every row go to F[4 ph + 2, 3]
     uint64_t *out;
     int64_t ostride;
     int m, W, b, wlo, whi, paired;
@@ -143,8 +144,13 @@ struct PairRows {
 __device__ __forceinline__ void pair_plain(const PairArgs &a, const PairSmem &S, const PairRows &R, int sub, int rg,
                                            int odd, int w0, bool v0, bool v1, int ja, int jb, bool check, bool &nzw)
 {
+    const bool cz = check;  // the zero-tail test proper
     const int pbase = R.R0 + rg, plast = a.m - 1;
     const bool idle = !v0 && !v1, both = v0 && v1;
+    // words b + 4 and b + 5 also go to the next pair's contiguous buffer (its front and pivot
+    // searches read them there), so that thread reads and writes every row
+    const bool fw = v0 && w0 == a.b + 4;
+    check = check || fw;
     auto pos = [&](int jj) { return min(max(pbase + jj * RPU, 0), plast); };
     int ph0 = 0, ph1 = 0, ph2 = 0, ph3 = 0, ph4 = 0, ph5 = 0;
     u64 zb0 = 0, zb1 = 0, zb2 = 0, zb3 = 0, zc0 = 0, zc1 = 0, zc2 = 0, zc3 = 0;
@@ -174,8 +180,13 @@ __device__ __forceinline__ void pair_plain(const PairArgs &a, const PairSmem &S,
             const int p = pbase + j * RPU;
             if (p < a.m && !idle && ((zb0 | zc0) != 0 || check)) {
                 const u64 n0 = d00 ^ x0, n1 = d01 ^ x1;
-                if (check)
+                if (cz)
                     nzw = nzw || (v0 && n0 != 0) || (v1 && n1 != 0);
+                if (fw) {
+                    a.F[4 * (int64_t)ph0 + 2] = n0;
+                    if (v1)
+                        a.F[4 * (int64_t)ph0 + 3] = n1;
+                }
                 if ((zb0 | zc0) != 0) {
                     uint64_t *dst = a.A + (int64_t)ph0 * a.stride + w0;
                     if (both) {
@@ -243,6 +254,11 @@ __device__ __forceinline__ void pair_general(const PairArgs &a, const PairSmem &
             row[0] = n0;
         if (v1)
             row[1] = n1;
+        if (v0 && w0 == a.b + 4) {
+            a.F[4 * (int64_t)ph + 2] = n0;
+            if (v1)
+                a.F[4 * (int64_t)ph + 3] = n1;
+        }
     } else if (kind && a.out) {
         uint64_t *row = a.out + (int64_t)p * a.ostride + w0;
         if (v0)
@@ -400,7 +416,8 @@ __device__ __forceinline__ int pair_row(const int *__restrict__ perm, const Pane
 __global__ void __launch_bounds__(NT, 1)
 k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, const PanelState *__restrict__ sb,
              const PanelState *__restrict__ sc, u64 *__restrict__ zb, u64 *__restrict__ zc,
-             uint64_t *__restrict__ out, int64_t ostride, int m, int W, int b)
+             const u64 *__restrict__ Fc, u64 *__restrict__ Fn, uint64_t *__restrict__ out, int64_t ostride, int m,
+             int W, int b)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     FrontSmem &S = *reinterpret_cast<FrontSmem *>(smraw);
@@ -425,25 +442,45 @@ k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, c
         for (int x = g; x < nxb; x += gs)
             perm[sb->xpos[x]] = sb->xval[x];
     }
-    if ((kb == 0 && kc == 0) || R0 + blockIdx.x * NT >= m)
-        return;  // no pivot: the words below are zero at b, b + 1 and unchanged right of them
+    if (R0 + blockIdx.x * NT >= m)
+        return;
+    if (kb == 0 && kc == 0) {
+        // no pivot: words b, b + 1 of every row below are zero; words b + 2, b + 3 pass to the next
+        // pair unchanged (zero too once the tail is known to be zero)
+        const bool zt = sb->zero_tail;
+        for (int p = R0 + g; p < m; p += gs) {
+            const int ph = pair_row(perm, sb, sc, R0, R1, nwb, nxb, nwc, nxc, p);
+            uint64_t *row = A + (int64_t)ph * stride + b;
+            row[0] = 0ull;
+            if (sc)
+                row[1] = 0ull;
+            if (sc && has2) {
+                Fn[4 * (int64_t)ph] = zt ? 0ull : Fc[4 * (int64_t)ph + 2];
+                if (has3)
+                    Fn[4 * (int64_t)ph + 1] = zt ? 0ull : Fc[4 * (int64_t)ph + 3];
+            }
+        }
+        return;
+    }
     // this thread's first row: its words are loaded while the tables are built
     int p = R0 + g, ph = -1;
     u64 w0 = 0, w1 = 0, w2 = 0, w3 = 0;
     if (p >= R1 && p < m) {
         ph = p < R2 ? sc->prow[p - R1] : pair_row(perm, sb, sc, R0, R1, nwb, nxb, nwc, nxc, p);
-        const uint64_t *row = A + (int64_t)ph * stride + b;
-        w0 = row[0];
+        const ulonglong2 *f = reinterpret_cast<const ulonglong2 *>(Fc + 4 * (int64_t)ph);
+        const ulonglong2 lo = f[0];
+        w0 = lo.x;
+        w1 = lo.y;
         if (p >= R2) {
-            w1 = has1 ? row[1] : 0ull;
-            w2 = has2 ? row[2] : 0ull;
-            w3 = has3 ? row[3] : 0ull;
+            const ulonglong2 hi = f[1];
+            w2 = hi.x;
+            w3 = hi.y;
         }
     }
     if (tid < 64) {
         const int t = tid;
-        const uint64_t *rb = A + (int64_t)(t < kb ? sb->prow[t] : 0) * stride + b;
-        const uint64_t *rc = A + (int64_t)(t < kc ? sc->prow[t] : 0) * stride + b;
+        const u64 *rb = Fc + 4 * (int64_t)(t < kb ? sb->prow[t] : 0);
+        const u64 *rc = Fc + 4 * (int64_t)(t < kc ? sc->prow[t] : 0);
         S.Xb[t] = t < kb ? sb->newblk[t] & sb->J & lowmask(sb->pcol[t] + 1) : 0ull;
         S.Ob[0][t] = t < kb && has1 ? rb[1] : 0ull;
         S.Ob[1][t] = t < kb && has2 ? rb[2] : 0ull;
@@ -507,13 +544,11 @@ k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, c
         if (ph < 0 && p >= R1) {
             // a later row of this thread (more rows than threads)
             ph = p < R2 ? sc->prow[p - R1] : pair_row(perm, sb, sc, R0, R1, nwb, nxb, nwc, nxc, p);
-            const uint64_t *row = A + (int64_t)ph * stride + b;
-            w0 = row[0];
-            if (p >= R2) {
-                w1 = has1 ? row[1] : 0ull;
-                w2 = has2 ? row[2] : 0ull;
-                w3 = has3 ? row[3] : 0ull;
-            }
+            const u64 *f = Fc + 4 * (int64_t)ph;
+            w0 = f[0];
+            w1 = f[1];
+            w2 = f[2];
+            w3 = f[3];
         }
         if (p < R1) {
             // pivot of panel b: its final words b .. b + 3
@@ -557,13 +592,24 @@ k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, c
                 n2 ^= bytesum(S.tab[M_E2C], v1);
                 n3 ^= bytesum(S.tab[M_E3C], v1);
             }
+            // words b + 2, b + 3 after both panels: the next pair's panel words, read by its pivot
+            // searches and its front from here (A gets them as multipliers then)
             if (has2)
-                row[2] = n2;
+                Fn[4 * (int64_t)ph] = n2;
             if (has3)
-                row[3] = n3;
+                Fn[4 * (int64_t)ph + 1] = n3;
         }
         ph = -1;
     }
+}
+
+// words 0 .. 3 of every row into the first pair's buffer
+__global__ void k_pair_init(const uint64_t *__restrict__ A, int64_t stride, u64 *__restrict__ F, int m, int W)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m)
+        for (int k = 0; k < 4; ++k)
+            F[4 * (int64_t)i + k] = k < W ? A[(int64_t)i * stride + k] : 0ull;
 }
 
 constexpr size_t PAIR_SMEM = sizeof(PairSmem);
@@ -573,8 +619,15 @@ constexpr size_t FRONT_SMEM = sizeof(FrontSmem);
 
 namespace gf2 {
 
-int launch_pivot_pair(const Elim &e, int b, const u64 *side_prev, int64_t side_stride, const PanelState *st_prev,
-                      PanelState *st, bool defer, bool programmatic, cudaStream_t s);
+int launch_pivot_pair(const Elim &e, int b, const u64 *wsrc, int64_t wstride, const u64 *side_prev,
+                      int64_t side_stride, const PanelState *st_prev, PanelState *st, bool defer, bool programmatic,
+                      cudaStream_t s);
+
+// the side region of the workspace: coordinates over panel b's and panel c's pivot rows (m each),
+// then two buffers of words b .. b + 3 of every row (4 m each), alternating with the pair
+static u64 *pair_zb(const Elim &e) { return e.side; }
+static u64 *pair_zc(const Elim &e) { return e.side + e.m; }
+static u64 *pair_F(const Elim &e, int b) { return e.side + 2 * e.m + (size_t)(((b >> 1) & 1) * 4) * e.m; }
 int init_states(const Elim &e, int nstates);
 
 static int sweep_pair(const Elim &e, int b, int wlo, int whi, bool paired, cudaStream_t s)
@@ -592,8 +645,9 @@ static int sweep_pair(const Elim &e, int b, int wlo, int whi, bool paired, cudaS
     a.perm = e.perm;
     a.sb = e.st + (b & 3);
     a.sc = e.st + ((b + 1) & 3);
-    a.zb = e.side;
-    a.zc = e.side + e.m;
+    a.zb = pair_zb(e);
+    a.zc = pair_zc(e);
+    a.F = pair_F(e, b + 2);
     a.out = e.out;
     a.ostride = e.ostride;
     a.m = (int)e.m;
@@ -629,7 +683,8 @@ static int pair_front(const Elim &e, int b, bool has_c, cudaStream_t s)
     const int grid = (int)(need < nsm ? (need > 0 ? need : 1) : nsm);
     const int tok = prof_begin(s);
     k_pair_front<<<grid, NT, FRONT_SMEM, s>>>(e.A, e.stride, e.perm, e.st + (b & 3), has_c ? e.st + ((b + 1) & 3) : nullptr,
-                                              e.side, e.side + e.m, e.out, e.ostride, (int)e.m, (int)e.W, b);
+                                              pair_zb(e), pair_zc(e), pair_F(e, b), pair_F(e, b + 2), e.out, e.ostride,
+                                              (int)e.m, (int)e.W, b);
     prof_end(s, GF2_PROF_COORDS, tok);
     prof_launched(1);
     return note_cuda(cudaGetLastError());
@@ -646,6 +701,10 @@ int elim_run_pair(const Elim &e, const ElimAux &aux)
     const int W = (int)e.W;
     if (W == 0)
         return GF2_OK;
+    k_pair_init<<<(int)((e.m + 255) / 256), 256, 0, e.s>>>(e.A, e.stride, pair_F(e, 0), (int)e.m, W);
+    prof_launched(1);
+    if ((rc = note_cuda(cudaGetLastError())))
+        return rc;
     cudaStream_t s = e.s, t = aux.side;
     cudaEvent_t ev_piv = aux.ev[0], ev_edge = aux.ev[1], ev_done = aux.ev[2];
     for (int b = 0; b < W; b += 2) {
@@ -654,9 +713,10 @@ int elim_run_pair(const Elim &e, const ElimAux &aux)
         const PanelState *sp = e.st + ((b + 3) & 3);  // panel b - 1 (slot 3, initialised, for b = 0)
         if (b >= 2 && (rc = note_cuda(cudaStreamWaitEvent(s, ev_edge, 0))))
             return rc;
-        if ((rc = launch_pivot_pair(e, b, nullptr, 0, sp, sb, false, false, s)))
+        const u64 *F = pair_F(e, b);  // words b .. b + 3 of every row
+        if ((rc = launch_pivot_pair(e, b, F, 4, nullptr, 0, sp, sb, false, false, s)))
             return rc;
-        if (has_c && (rc = launch_pivot_pair(e, b + 1, reinterpret_cast<const u64 *>(e.A) + b, e.stride, sb, sc, true, true, s)))
+        if (has_c && (rc = launch_pivot_pair(e, b + 1, F + 1, 4, F, 4, sb, sc, true, true, s)))
             return rc;
         if ((rc = note_cuda(cudaEventRecord(ev_piv, s))) || (rc = note_cuda(cudaStreamWaitEvent(t, ev_piv, 0))))
             return rc;

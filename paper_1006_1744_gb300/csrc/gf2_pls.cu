@@ -127,11 +127,10 @@ struct PivotShared {
 // word b only in its side buffer, so the pivot search derives it from A
 // (current up to panel b - 2) plus panel b - 1's contribution.
 struct WordCtx {
-    const uint64_t *A;
-    int64_t stride;
-    const u64 *side_prev;  // panel word b - 1 of every row (nullptr: A's word b is already current)
-    int64_t side_stride;   // words between consecutive rows of side_prev (1, or A's row pitch)
-    int b;
+    const uint64_t *wsrc;  // word b of row 0 (A + b, or a buffer of the rows' panel words) ...
+    int64_t wstride;       // ... and the words between consecutive rows there
+    const u64 *side_prev;  // panel word b - 1 of every row (nullptr: wsrc's word b is already current)
+    int64_t side_stride;   // words between consecutive rows of side_prev
 };
 
 // word b of a row from its value in A and its panel word b - 1 (v)
@@ -149,7 +148,7 @@ __device__ __forceinline__ u64 word_after(const PivotShared &S, u64 w, u64 v)
 
 __device__ __forceinline__ u64 panel_word(const WordCtx &c, const PivotShared &S, int ph)
 {
-    const u64 w = c.A[(int64_t)ph * c.stride + c.b];
+    const u64 w = c.wsrc[(int64_t)ph * c.wstride];
     return c.side_prev ? word_after(S, w, c.side_prev[(int64_t)ph * c.side_stride]) : w;
 }
 
@@ -600,7 +599,7 @@ static_assert(WIN <= PIVOT_THREADS, "one window row per thread when the window i
 // sweep has completed: the zero-tail test reads it. defer_prev: panel b - 1's
 // row order is left out of perm (a sweep still running reads those positions
 // there; the step after this search applies it) and taken from st_prev here.
-__device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int64_t stride,
+__device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ wsrc, int64_t wstride,
                                             const u64 *__restrict__ side_prev, int64_t side_stride,
                                             int *__restrict__ perm, const PanelState *__restrict__ st_prev,
                                             PanelState *st, int64_t *P, int64_t *Q, int m, int b, int nbits,
@@ -619,7 +618,7 @@ __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int6
     const int nwin = (r < m && !zt) ? min(WIN, m - r) : 0;
     // panel b - 1's contribution to word b is added here unless A holds it already
     const bool contrib = b > 0 && side_prev != nullptr;
-    const WordCtx wc{A, stride, contrib ? side_prev : nullptr, side_stride, b};
+    const WordCtx wc{wsrc, wstride, contrib ? side_prev : nullptr, side_stride};
     // window rows: the previous panel's order where it changed it, perm elsewhere
     // (one row per thread; nwin <= PIVOT_THREADS)
     int ph = 0;
@@ -638,7 +637,7 @@ __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int6
                 if (ph < 0)
                     ph = perm[p];
             }
-            w = A[(int64_t)ph * stride + b];
+            w = wsrc[(int64_t)ph * wstride];
             if (contrib)
                 v = side_prev[(int64_t)ph * side_stride];
         }
@@ -659,7 +658,7 @@ __device__ __forceinline__ void pivot_panel(const uint64_t *__restrict__ A, int6
     }
     if (contrib && tid < 64) {
         S.pZ[tid] = st_prev->zmap[tid];
-        S.pO[tid] = tid < st_prev->kbar ? A[(int64_t)st_prev->prow[tid] * stride + b] : 0ull;
+        S.pO[tid] = tid < st_prev->kbar ? wsrc[(int64_t)st_prev->prow[tid] * wstride] : 0ull;
     }
     if (tid == 0) {
         S.nx = 0;
@@ -847,20 +846,20 @@ k_pivot(const uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ 
 {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    pivot_panel(A, stride, side_prev, 1, perm, st_prev, st, P, Q, m, b, nbits, form, thr_permille);
+    pivot_panel(A + b, stride, side_prev, 1, perm, st_prev, st, P, Q, m, b, nbits, form, thr_permille);
 }
 
 // Pivot search of one panel of a two-panel sweep step (gf2_pair.cu): states in four slots,
 // the previous panel's word from side_prev with any row pitch, its row order optionally
 // deferred. Programmatic dependent of the preceding search, as k_pivot.
 __global__ void __launch_bounds__(PIVOT_THREADS, 1)
-k_pivot_pair(const uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_prev, int64_t side_stride,
-             int *__restrict__ perm, const PanelState *__restrict__ st_prev, PanelState *st, int64_t *P, int64_t *Q,
-             int m, int b, int nbits, int defer)
+k_pivot_pair(const uint64_t *__restrict__ wsrc, int64_t wstride, const u64 *__restrict__ side_prev,
+             int64_t side_stride, int *__restrict__ perm, const PanelState *__restrict__ st_prev, PanelState *st,
+             int64_t *P, int64_t *Q, int m, int b, int nbits, int defer)
 {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    pivot_panel(A, stride, side_prev, side_stride, perm, st_prev, st, P, Q, m, b, nbits, 0, 0, 4, defer != 0);
+    pivot_panel(wsrc, wstride, side_prev, side_stride, perm, st_prev, st, P, Q, m, b, nbits, 0, 0, 4, defer != 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -1383,7 +1382,7 @@ __global__ void __launch_bounds__(PIVOT_THREADS, 1) k_pivot_b(const gf2::ElimDes
 {
     const gf2::ElimDesc &d = D[idx[blockIdx.x]];
     const int nbits = min(64, d.n - 64 * b);
-    pivot_panel(d.A, d.stride, d.side + (size_t)((b + 1) & 1) * d.m, 1, d.perm, d.st + ((b + 1) & 1), d.st + (b & 1),
+    pivot_panel(d.A + b, d.stride, d.side + (size_t)((b + 1) & 1) * d.m, 1, d.perm, d.st + ((b + 1) & 1), d.st + (b & 1),
                 d.P, d.Q, d.m, b, nbits, 0, 0);
 }
 
@@ -1535,7 +1534,7 @@ __device__ bool team_eliminate(SweepSmem &S, const gf2::ElimDesc &d, int tr, int
         return false;
     for (int b = 0; b < W; ++b) {
         if (tr == 0 && tid < PIVOT_THREADS)
-            pivot_panel(d.A, d.stride, d.side + (size_t)((b + 1) & 1) * m, 1, d.perm, d.st + ((b + 1) & 1),
+            pivot_panel(d.A + b, d.stride, d.side + (size_t)((b + 1) & 1) * m, 1, d.perm, d.st + ((b + 1) & 1),
                         d.st + (b & 1), d.P, d.Q, m, b, min(64, d.n - 64 * b), 0, 0);
         if (!team_barrier(bar, target, G, pl))
             return false;
@@ -1815,8 +1814,9 @@ int elim_run(const Elim &e)
     return elim_run(e, aux);
 }
 
-int launch_pivot_pair(const Elim &e, int b, const u64 *side_prev, int64_t side_stride, const PanelState *st_prev,
-                      PanelState *st, bool defer, bool programmatic, cudaStream_t s)
+int launch_pivot_pair(const Elim &e, int b, const u64 *wsrc, int64_t wstride, const u64 *side_prev,
+                      int64_t side_stride, const PanelState *st_prev, PanelState *st, bool defer, bool programmatic,
+                      cudaStream_t s)
 {
     const int nbits = (int)((e.n - 64ll * b) < 64 ? (e.n - 64ll * b) : 64);
     cudaLaunchConfig_t cfg = {};
@@ -1829,7 +1829,7 @@ int launch_pivot_pair(const Elim &e, int b, const u64 *side_prev, int64_t side_s
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const int tok = prof_begin(s);
-    int rc = note_cuda(cudaLaunchKernelEx(&cfg, k_pivot_pair, (const uint64_t *)e.A, e.stride, side_prev, side_stride,
+    int rc = note_cuda(cudaLaunchKernelEx(&cfg, k_pivot_pair, (const uint64_t *)wsrc, wstride, side_prev, side_stride,
                                           e.perm, st_prev, st, e.P, e.Q, (int)e.m, b, nbits, defer ? 1 : 0));
     prof_end(s, GF2_PROF_PIVOT, tok);
     prof_launched(1);
