@@ -370,8 +370,11 @@ struct FrontSmem {
     u64 Ob[3][64];       // panel b's pivot rows at words b + 1, b + 2, b + 3
     u64 Oc[3][64];       // panel c's pivot rows: word b (raw), then words b + 2, b + 3 after panel b
     u64 zmb[64], zmc[64];  // the panels' zmaps
+    // 4-bit tables (16 positions x 16 values) of the sums of rows of Xb, Ob[0..2], zmb, Xc, Oc[1..2]
+    u64 nib[8][256];
     int sc_[6];          // r_cur, kbar of panel b, kbar of panel c, window and swaps of b and c
 };
+enum { N_XB, N_OB0, N_OB1, N_OB2, N_ZMB, N_XC, N_OC1, N_OC2 };
 
 __device__ __forceinline__ u64 bytesum(const u64 *__restrict__ t, u64 w)
 {
@@ -382,14 +385,29 @@ __device__ __forceinline__ u64 bytesum(const u64 *__restrict__ t, u64 w)
     return a;
 }
 
-// sum of src[s] over the set bits s of z (64 independent loads, four XOR chains)
-__device__ __forceinline__ u64 select_sum(u64 z, const u64 *__restrict__ src)
+// sum of the 64 rows src[0..63] selected by the set bits of z, through its 4-bit table (sixteen
+// lookups, two XOR chains)
+__device__ __forceinline__ u64 select_sum(u64 z, const u64 *__restrict__ nib)
 {
-    u64 a[4] = {0ull, 0ull, 0ull, 0ull};
+    u64 a0 = 0, a1 = 0;
 #pragma unroll
-    for (int s2 = 0; s2 < 64; ++s2)
-        a[s2 & 3] ^= ((z >> s2) & 1ull) ? src[s2] : 0ull;
-    return (a[0] ^ a[1]) ^ (a[2] ^ a[3]);
+    for (int q = 0; q < 16; q += 2) {
+        a0 ^= nib[q * 16 + (int)((z >> (4 * q)) & 15u)];
+        a1 ^= nib[(q + 1) * 16 + (int)((z >> (4 * q + 4)) & 15u)];
+    }
+    return a0 ^ a1;
+}
+
+// 4-bit tables of 64 rows: entry (q, v) = the sum of rows 4 q + j for the set bits j of v. Lane l
+// of a warp writes entries l and l + 32 of a table (consecutive lanes, consecutive entries).
+__device__ __forceinline__ void build_nib(u64 *__restrict__ nib, const u64 *__restrict__ src, int e)
+{
+    const int q = e >> 4, v = e & 15;
+    u64 a = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        a ^= ((v >> j) & 1) ? src[4 * q + j] : 0ull;
+    nib[e] = a;
 }
 
 // Physical row at trailing position p >= R2 of a pair: panel c's order, else panel b's, else perm
@@ -434,7 +452,9 @@ k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, c
     const int R0 = S.sc_[0], R1 = R0 + kb, R2 = R1 + kc;
     const int nwb = S.sc_[3], nxb = S.sc_[4], nwc = S.sc_[5] >> 8, nxc = S.sc_[5] & 255;
     const bool has1 = b + 1 < W, has2 = b + 2 < W, has3 = b + 3 < W;
-    const int g = blockIdx.x * NT + tid, gs = gridDim.x * NT;
+    // consecutive positions go to different CTAs, so the pivot rows (the first positions, whose
+    // rows cost most here) spread over the grid
+    const int g = tid * gridDim.x + blockIdx.x, gs = gridDim.x * NT;
     // panel b's row order into perm (its pivot search of panel c left it out)
     if (sc) {
         for (int i = g; i < nwb; i += gs)
@@ -442,7 +462,7 @@ k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, c
         for (int x = g; x < nxb; x += gs)
             perm[sb->xpos[x]] = sb->xval[x];
     }
-    if (R0 + blockIdx.x * NT >= m)
+    if (R0 + (int)blockIdx.x >= m)
         return;
     if (kb == 0 && kc == 0) {
         // no pivot: words b, b + 1 of every row below are zero; words b + 2, b + 3 pass to the next
@@ -491,28 +511,35 @@ k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, c
         S.Oc[2][t] = t < kc && has3 ? rc[3] : 0ull;
     }
     __syncthreads();
+    for (int e = tid; e < 6 * 256; e += NT) {
+        const int k = e >> 8;
+        const u64 *src = k == N_XB ? S.Xb : k == N_ZMB ? S.zmb : k == N_XC ? S.Xc : S.Ob[k - N_OB0];
+        build_nib(S.nib[k], src, e & 255);
+    }
+    __syncthreads();
     if (tid < 5 * 64) {
         // panel b's maps: bit i of word b -> ...
         const int mp = tid >> 6, i = tid & 63;
         const u64 zm = S.zmb[i];
-        const u64 *src = mp == 1 ? S.Xb : mp == 2 ? S.Ob[0] : mp == 3 ? S.Ob[1] : S.Ob[2];
-        S.img[mp][i] = mp == 0 ? zm : select_sum(zm, src);
+        S.img[mp][i] = mp == 0 ? zm : select_sum(zm, S.nib[mp == 1 ? N_XB : N_OB0 + mp - 2]);
     } else if (tid < 5 * 64 + 64) {
         // panel c's pivot rows at words b + 2, b + 3 after panel b (their coordinates over O_b
         // from their word b)
         const int t = tid - 5 * 64;
         if (t < kc) {
-            const u64 zt = select_sum(S.Oc[0][t], S.zmb);
-            S.Oc[1][t] ^= select_sum(zt, S.Ob[1]);
-            S.Oc[2][t] ^= select_sum(zt, S.Ob[2]);
+            const u64 zt = select_sum(S.Oc[0][t], S.nib[N_ZMB]);
+            S.Oc[1][t] ^= select_sum(zt, S.nib[N_OB1]);
+            S.Oc[2][t] ^= select_sum(zt, S.nib[N_OB2]);
         }
     }
+    __syncthreads();
+    for (int e = tid; e < 2 * 256; e += NT)
+        build_nib(S.nib[N_OC1 + (e >> 8)], S.Oc[1 + (e >> 8)], e & 255);
     __syncthreads();
     if (tid < 4 * 64) {
         const int mp = tid >> 6, i = tid & 63;
         const u64 zm = S.zmc[i];
-        const u64 *src = mp == 1 ? S.Xc : mp == 2 ? S.Oc[1] : S.Oc[2];
-        S.img[M_ZC + mp][i] = mp == 0 ? zm : select_sum(zm, src);
+        S.img[M_ZC + mp][i] = mp == 0 ? zm : select_sum(zm, S.nib[mp == 1 ? N_XC : N_OC1 + mp - 2]);
     }
     __syncthreads();
     {
@@ -558,11 +585,11 @@ k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, c
                 const u64 zt = sb->zpiv[t];
                 o[0] = sb->newblk[t];
                 if (has1)
-                    o[1] = select_sum(zt, S.Ob[0]);
+                    o[1] = select_sum(zt, S.nib[N_OB0]);
                 if (has2)
-                    o[2] = select_sum(zt, S.Ob[1]);
+                    o[2] = select_sum(zt, S.nib[N_OB1]);
                 if (has3)
-                    o[3] = select_sum(zt, S.Ob[2]);
+                    o[3] = select_sum(zt, S.nib[N_OB2]);
             }
         } else if (p < R2) {
             // pivot of panel c: panel b's multipliers in A, its final words b + 1 .. b + 3
@@ -575,9 +602,9 @@ k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, c
                 const u64 zt = sc->zpiv[t];
                 o[1] = sc->newblk[t];
                 if (has2)
-                    o[2] = select_sum(zt, S.Oc[1]);
+                    o[2] = select_sum(zt, S.nib[N_OC1]);
                 if (has3)
-                    o[3] = select_sum(zt, S.Oc[2]);
+                    o[3] = select_sum(zt, S.nib[N_OC2]);
             }
         } else {
             uint64_t *row = A + (int64_t)ph * stride + b;
