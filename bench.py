@@ -579,10 +579,20 @@ def run_config5(args):
 
 def sweep_algorithmic_bytes(Q, m: int, W: int, r: int) -> float:
     """Read + write bytes of the trailing blocks of all panels: panel b sweeps the (m - r_b) x (W - b)
-    trailing words, r_b = pivots left of column 64 b ((m - r)(n - c)/4 per panel)."""
+    trailing words, r_b = pivots left of column 64 b ((m - r)(n - c)/4 bytes per sweep of 64 columns)."""
     import numpy as np
     rb = np.searchsorted(np.asarray(Q[:r]), 64 * np.arange(W))
     return float(np.sum((m - rb).clip(min=0) * (W - np.arange(W)) * 16.0))
+
+
+def pair_sweep_algorithmic_bytes(Q, m: int, W: int, r: int) -> float:
+    """Two panels per sweep: the sweep of panels b, b + 1 (b even) streams words b + 4 .. W - 1 of the
+    rows from position r_b on (words b .. b + 3 are its front's), read + write: (m - r_b)(W - b - 4) x 16."""
+    import numpy as np
+    b = np.arange(0, W, 2)
+    b = b[b + 4 < W]
+    rb = np.searchsorted(np.asarray(Q[:r]), 64 * b)
+    return float(np.sum((m - rb).clip(min=0) * (W - b - 4) * 16.0))
 
 
 def side_numbers_16384(g, dev, steps: int):
@@ -713,23 +723,30 @@ def run_headline(args):
     sweep_ms, sweep_n = gf2.prof_collect(gf2.PROF_SWEEP)
     pivot_ms, pivot_n = gf2.prof_collect(gf2.PROF_PIVOT)
     rref_blk_ms, rref_blk_n = gf2.prof_collect(gf2.PROF_RREF)
+    front_ms, front_n = gf2.prof_collect(gf2.PROF_COORDS)
     gf2.prof_reset()
+    pair = front_n > 0  # two panels per sweep ran (the library's choice at this size, or --panels-per-sweep 2)
 
     step_ms_max = max_over_ranks(step_ms, world, dev)
     rank_val = int(r1.item())
     if with_rref:
         assert rank_val == int(r2.item())
     elims = 2 if with_rref else 1  # gf2_rref's PLS route runs the elimination too
-    sweep_bytes = sweep_algorithmic_bytes(Q.cpu().numpy(), m, W, rank_val) * elims * prof_steps
+    bytes_fn = pair_sweep_algorithmic_bytes if pair else sweep_algorithmic_bytes
+    sweep_bytes = bytes_fn(Q.cpu().numpy(), m, W, rank_val) * elims * prof_steps
     hbm, peak_kind = peaks()
     shares = {"sweep": sweep_ms, "pivot": pivot_ms, "rref_block": rref_blk_ms}
+    if pair:
+        shares["front"] = front_ms
     tot = sum(shares.values()) or 1.0
     dominant = max(shares, key=shares.get)
     achieved = sweep_bytes / (sweep_ms * 1e-3) / 1e9 if sweep_ms > 0 else 0.0
     bytes_per_launch = sweep_bytes / max(sweep_n, 1)
-    prof_name = f"k_sweep16_{n}"
+    prof_name = f"k_pair_sweep_{n}" if pair else f"k_sweep16_{n}"
     traffic_ratio = traffic_from_profiles(prof_name)
-    roofline = {"kernel": "k_sweep16 (table sweep: MakeTable1 + AddRowsFromTable)", "bound": "hbm",
+    kname = ("k_pair_sweep (table sweep of two panels: MakeTable1 + AddRowsFromTable over 128 pivot columns)"
+             if pair else "k_sweep16 (table sweep: MakeTable1 + AddRowsFromTable)")
+    roofline = {"kernel": kname, "bound": "hbm",
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst)" if peak_kind == "measured"
                 else peak_kind,
@@ -738,12 +755,18 @@ def run_headline(args):
                                 "x the average launch's algorithmic bytes" if traffic_ratio else "no capture",
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_us": sweep_ms * 1e3 / max(sweep_n, 1),
-                "note": "bytes per panel = (m - r_b)(W - b) x 16 (read + write of the trailing words); "
+                "note": ("bytes per sweep of panels b, b + 1 = (m - r_b)(W - b - 4) x 16 (read + write of the "
+                         "trailing words right of the front's four); half the DRAM traffic per panel of one "
+                         "sweep per panel, at the same shared-memory lookups per panel, so the kernel is bound "
+                         "by the L1/shared-memory data port (profiles/k_pair_sweep_*.md) before DRAM; "
+                         if pair else "bytes per panel = (m - r_b)(W - b) x 16 (read + write of the trailing "
+                         "words); ")
                         + ("the matrix is L2-resident within a step" if not big else "input larger than L2")}
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     pivot_us = pivot_ms * 1e3 / max(pivot_n, 1)
     floor_us = 64 * (26 + 38) / sm_mhz
-    pivot_chain = {"kernel": "k_pivot (panel pivot search: PlsSubmatrix)", "bound": "latency",
+    pivot_chain = {"kernel": ("k_pivot_pair" if pair else "k_pivot") + " (panel pivot search: PlsSubmatrix)",
+                   "bound": "latency",
                    "avg_launch_us": pivot_us, "chain_floor_us": floor_us,
                    "frac": floor_us / pivot_us if pivot_us else 0.0,
                    "note": "1 CTA; the elimination chain of 64 pivots (warp min-reduction 26 cycles + 64-bit "
@@ -811,7 +834,7 @@ def run_headline(args):
         "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": f"{n}x{n} dense Bernoulli(1/2) GF(2): {what}; MMPF panels with XOR-table "
-                               f"sweeps (k = 8 per table, 64 pivots per sweep)",
+                               f"sweeps (k = 8 per table, {128 if pair else 64} pivots per sweep)",
                    "m": m, "n": n, "seed": SEED, "parallelism": f"replicas x{world}",
                    "l2": ("input (512 MB) larger than L2; restored from a pristine copy before each step, "
                           "outside the timed events") if big else
@@ -821,7 +844,8 @@ def run_headline(args):
         "wall_s_timed_region": wall,
         "roofline": roofline, "pivot_chain": pivot_chain,
         "kernel_time_shares": {k: v / tot for k, v in shares.items()}, "dominant_kernel": dominant,
-        "kernel_launches": {"sweep": sweep_n, "pivot": pivot_n, "rref_block": rref_blk_n, "steps": prof_steps},
+        "kernel_launches": {"sweep": sweep_n, "pivot": pivot_n, "rref_block": rref_blk_n, "front": front_n,
+                            "steps": prof_steps},
         "gpu_launches": launches,
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "paper_context": PAPER_CONTEXT,
     }

@@ -100,11 +100,20 @@ extern "C" int gf2_autotune(int op, int64_t m, int64_t n, double density, gf2_op
             cands.push_back(opt(0, 0, GF2_PRODUCT_STRASSEN_TENSOR));
         }
     } else {
-        for (int tw : {4, 8, 16})
-            cands.push_back(opt(tw, 0, 0));
+        for (int tw : {4, 8, 16}) {
+            gf2_opts o = opt(tw, 0, 0);
+            o.panels_per_sweep = 1;  // the tile width is the one-panel sweep's
+            cands.push_back(o);
+        }
         {
             gf2_opts o = opt(16, 0, 0);  // 4-bit tables (Sec. 3.1's k) on the 16-word sweep
             o.k = 4;
+            o.panels_per_sweep = 1;
+            cands.push_back(o);
+        }
+        for (int pps : {1, 2}) {
+            gf2_opts o = opt(0, 0, 0);  // one panel per sweep, or two (gf2_pair.cu)
+            o.panels_per_sweep = pps;
             cands.push_back(o);
         }
         if (op == GF2_OP_RREF) {

@@ -317,4 +317,5 @@ def autotune(op: int, m: int, n: int, density: float = 0.5, stream=None):
     _check(lib().gf2_autotune(op, m, n, float(density), ctypes.byref(best), ctypes.byref(ms), _stream(stream)),
            "gf2_autotune")
     return {"k": best.k, "tile_words": best.tile_words, "cutoff_cols": best.cutoff_cols, "product": best.product,
-            "rref_method": best.rref_method, "hybrid_permille": best.hybrid_permille}, ms.value
+            "rref_method": best.rref_method, "hybrid_permille": best.hybrid_permille,
+            "panels_per_sweep": best.panels_per_sweep}, ms.value

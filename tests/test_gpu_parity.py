@@ -614,7 +614,8 @@ def test_autotune_choices_are_exact_and_cached(g):
     choice matches the oracle, and a second call returns the cached choice."""
     m, n = 1500, 2100
     o1, ms1 = g.autotune(g.OP_PLS, m, n, 0.5)
-    assert o1["tile_words"] in (4, 8, 16) and ms1 > 0
+    # a tile width of the one-panel sweep, or one or two panels per sweep at the default tiles
+    assert (o1["tile_words"] in (4, 8, 16) or o1["panels_per_sweep"] in (1, 2)) and ms1 > 0
     o2, ms2 = g.autotune(g.OP_PLS, m, n, 0.5)
     assert (o1, ms1) == (o2, ms2)
     check_pls(g, S.dense(m, n, 77), m, n, opts=o1)
