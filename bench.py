@@ -286,8 +286,8 @@ def run_config3(args):
     dev = torch.device("cuda", 0)
     A0 = torch.empty((n, st), dtype=torch.int64, device=dev)
     A = torch.empty_like(A0)
-    methods = {"mmpf": None, "rec_xor": {"cutoff_cols": 4096, "product": 1},
-               "rec_tc": {"cutoff_cols": 4096, "product": 2}}
+    methods = {"mmpf": None, "mmpf_1panel": {"panels_per_sweep": 1},
+               "rec_xor": {"cutoff_cols": 4096, "product": 1}, "rec_tc": {"cutoff_cols": 4096, "product": 2}}
     steps = max(1, min(args.steps, 3))
     results = {}
     checks = {}
@@ -316,13 +316,15 @@ def run_config3(args):
             Qb = torch.empty(n, dtype=torch.int64, device=dev)
             ms = _timed(lambda: gf2.pls(A, n, Q=Qb, rank=rank, opts=o), steps, 1, pre=lambda: A.copy_(A0))
             results[variant][name] = {"ms": ms, "rank": int(rank.item())}
-            if name == "mmpf":
-                # the panel sweeps' algorithmic bytes (read + write of every panel's trailing
-                # block) over the whole elimination's time: a lower bound on the sweeps' HBM rate
+            if name in ("mmpf", "mmpf_1panel"):
+                # the sweeps' algorithmic bytes (read + write of every sweep's trailing block: one
+                # sweep per panel, or per two panels at this size by default) over the whole
+                # elimination's time: a lower bound on the sweeps' HBM rate
                 rv = int(rank.item())
                 W = (n + 63) // 64
-                rb = np.searchsorted(Qb[:rv].cpu().numpy(), 64 * np.arange(W))
-                byts = float(np.sum((n - rb).clip(min=0) * (W - np.arange(W)) * 16.0))
+                Qh = Qb[:rv].cpu().numpy()
+                byts = (sweep_algorithmic_bytes(Qh, n, W, rv) if name == "mmpf_1panel"
+                        else pair_sweep_algorithmic_bytes(Qh, n, W, rv))
                 hbm, _ = peaks()
                 gbs = byts / (ms * 1e-3) / 1e9
                 results[variant][name].update({"sweep_algorithmic_GB": byts / 1e9, "sweep_GBps_over_elimination": gbs,
@@ -341,7 +343,8 @@ def run_config3(args):
     gf2.prof_enable(0)
     clocks = sampler.stop()
     best = results["dense"]["mmpf"]["ms"]
-    speed = {v: {"rec_tc_over_rec_xor": r["rec_xor"]["ms"] / r["rec_tc"]["ms"],
+    speed = {v: {"two_panels_over_one": r["mmpf_1panel"]["ms"] / r["mmpf"]["ms"],
+                 "rec_tc_over_rec_xor": r["rec_xor"]["ms"] / r["rec_tc"]["ms"],
                  "mmpf_over_rec_xor": r["rec_xor"]["ms"] / r["mmpf"]["ms"],
                  "mmpf_over_rec_tc": r["rec_tc"]["ms"] / r["mmpf"]["ms"]} for v, r in results.items()}
     _base_line(args, best / 1e3, "s", best,
