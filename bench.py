@@ -54,18 +54,23 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def traffic_from_profiles(name: str):
-    """DRAM bytes over algorithmic bytes of one ncu-captured launch of a kernel, as recorded in
-    profiles/<name>.md (a line "traffic_ratio: X"); None if there is no such capture."""
+def profile_value(name: str, key: str):
+    """A figure of one ncu-captured launch of a kernel, as recorded in profiles/<name>.md (a line
+    "<key>: X"); None if there is no such capture or line."""
     path = os.path.join(ROOT, "profiles", f"{name}.md")
     try:
         for line in open(path):
-            if line.startswith("traffic_ratio:"):
+            if line.startswith(key + ":"):
                 v = line.split(":", 1)[1].strip()
                 return None if v in ("", "null") else float(v)
     except OSError:
         pass
     return None
+
+
+def traffic_from_profiles(name: str):
+    """DRAM bytes over algorithmic bytes of one ncu-captured launch ("traffic_ratio")."""
+    return profile_value(name, "traffic_ratio")
 
 
 class ClockSampler:
@@ -477,12 +482,19 @@ def run_config5(args):
     SPLIT = 8192
     classes = [[i for i in range(R) if rec[i][0] < SPLIT], [i for i in range(R) if rec[i][0] >= SPLIT]]
     shares = (0.25, 0.75)
+    single = args.large_lane_cap == 1  # large requests one at a time through gf2_pls
+    if single:
+        gf2.replay_enable(0)  # every request has its own buffers: no graph is worth capturing
+        for i in classes[1]:
+            ws_each[i] = gf2.workspace_bytes(gf2.OP_PLS, rec[i][0], rec[i][1])
     lanes = []
     for c, share in zip(classes, shares):
         need = gf2.pls_batched_workspace_bytes([shapes[i] for i in c]) if c else 0
         bud = int(min(total_budget * share, need)) if c else 0
         bud = max(bud, max((ws_each[i] for i in c), default=0))
         lanes.append({"ids": c, "budget": bud, "stream": torch.cuda.Stream(device=dev),
+                      "cap": (args.large_lane_cap or R) if share == shares[1] else R,
+                      "single": single and share == shares[1],
                       "work": torch.empty(max(bud, 256) // 8 + 64, dtype=torch.int64, device=dev)})
     opts = {"batch_mode": gf2.BATCH_STEPS}
 
@@ -491,8 +503,13 @@ def run_config5(args):
             for i in ids:
                 mats[i].copy_(mats0[i])
             rk = torch.empty(len(ids), dtype=torch.int64, device=dev)
-            gf2.pls_batched([mats[i] for i in ids], [ns[i] for i in ids], [Ps[i] for i in ids],
-                            [Qs[i] for i in ids], rk, work=lane["work"], opts=opts, stream=lane["stream"])
+            if lane.get("single"):
+                # one request: the single-matrix pipeline (look-ahead pivot searches beside the sweeps)
+                i = ids[0]
+                gf2.pls(mats[i], ns[i], P=Ps[i], Q=Qs[i], rank=rk[0:1], work=lane["work"], stream=lane["stream"])
+            else:
+                gf2.pls_batched([mats[i] for i in ids], [ns[i] for i in ids], [Ps[i] for i in ids],
+                                [Qs[i] for i in ids], rk, work=lane["work"], opts=opts, stream=lane["stream"])
             ev = torch.cuda.Event()
             ev.record(lane["stream"])
         return rk, ev
@@ -521,8 +538,14 @@ def run_config5(args):
                 c = L["ids"]
                 ids, need = [], 0
                 k = st["next"]
+                cap = L["cap"]
+                if cap < 0:
+                    # adaptive: small batches while few requests wait (latency), larger ones as the
+                    # queue grows (throughput)
+                    waiting = int(np.searchsorted(arr[c[k:]], now, side="right")) if k < len(c) else 0
+                    cap = max(-cap, waiting // 2)
                 while k < len(c) and arr[c[k]] <= now:
-                    if ids and need + ws_each[c[k]] > L["budget"]:
+                    if ids and (need + ws_each[c[k]] > L["budget"] or len(ids) >= cap):
                         break
                     ids.append(c[k])
                     need += ws_each[c[k]]
@@ -573,6 +596,7 @@ def run_config5(args):
                             "arrivals at 0.5, 0.8, 1.0 x capacity, batched as they arrive in two lanes (m < 8192, "
                             "m >= 8192), PLS + rank",
                 "requests": R, "seed": SEED, "value_is": "p99 latency at 0.8 x capacity",
+                "large_lane_cap": args.large_lane_cap or None,
                 "workspace_budget_bytes": [L["budget"] for L in lanes]},
                clocks, launches,
                {"capacity_per_s": capacity, "by_load": results, "rank_sum": int(ranks.sum().item()),
@@ -758,6 +782,10 @@ def run_headline(args):
                                 "x the average launch's algorithmic bytes" if traffic_ratio else "no capture",
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_us": sweep_ms * 1e3 / max(sweep_n, 1),
+                "binding_unit": {"unit": "L1/shared-memory data port (l1tex throughput, pct of peak)",
+                                 "frac": profile_value(prof_name, "l1_port_frac"),
+                                 "source": f"profiles/{prof_name}.md (one captured launch)"}
+                if pair else None,
                 "note": ("bytes per sweep of panels b, b + 1 = (m - r_b)(W - b - 4) x 16 (read + write of the "
                          "trailing words right of the front's four); half the DRAM traffic per panel of one "
                          "sweep per panel, at the same shared-memory lookups per panel, so the kernel is bound "
@@ -877,6 +905,9 @@ def main():
     ap.add_argument("--variants", action="store_true",
                     help="config 3: the three 65536^2 matrices through MMPF and the recursive PLS")
     ap.add_argument("--requests", type=int, default=4096, help="config 5: requests per arrival rate")
+    ap.add_argument("--large-lane-cap", type=int, default=0,
+                    help="config 5: most requests per batch of the large lane (0: no cap; -k: at least k, "
+                         "else half of those waiting)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

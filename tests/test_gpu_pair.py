@@ -127,3 +127,29 @@ def test_pair_replayed_calls_with_new_contents(g):
         assert (P.cpu().numpy() == Pw).all() and (Q.cpu().numpy() == Qw).all()
         W = S.words_per_row(n)
         assert (host(D)[:, :W] == R[:, :W]).all()
+
+
+def test_pair_more_rows_than_front_threads(g):
+    """More rows than the front kernel has threads (152 CTAs x 512): each thread takes a
+    second row after the tables are built."""
+    for kind, (m, n) in (("dense", (100000, 300)), ("lowrank", (90000, 200)), ("echelon", (81000, 450))):
+        A = make(kind, m, n, 5600 + n)
+        check_pls(g, A, m, n, PAIR)
+
+
+def test_pair_wide_stride_and_caller_workspace(g):
+    """A row pitch above the minimum and a workspace of exactly gf2_workspace_bytes."""
+    m, n = 1500, 1900
+    st = S.default_stride(n) + 32
+    A = make("dense", m, n, 5700, stride=st)
+    R, P, Q, r = oracle.pls(A, m, n)
+    need = g.workspace_bytes(g.OP_PLS, m, n, PAIR)
+    work = torch.empty(need // 8 + 32, dtype=torch.int64, device="cuda")
+    D = dev(A)
+    Pd, Qd, rd = g.pls(D, n, work=work, opts=PAIR)
+    torch.cuda.synchronize()
+    assert int(rd.item()) == r
+    assert (Pd.cpu().numpy() == P).all() and (Qd.cpu().numpy() == Q).all()
+    W = S.words_per_row(n)
+    assert (host(D)[:, :W] == R[:, :W]).all()
+    assert (host(D)[:, W:] == A[:, W:]).all(), "words past the row's last word were written"
