@@ -804,47 +804,83 @@ def run_headline(args):
                            "shuffle 38 cycles per pivot), plus window formation and the inverses"}
 
     # ---- end to end through the C ABI: pinned host buffers, copies inside the timed region ---
+    # Every step copies its input in from pinned host memory, runs the elimination and copies its
+    # results out. Two sets of buffers alternate, with the copies on streams of their own, so step
+    # i + 1's input copy and step i - 1's result copy overlap step i's elimination (the way a
+    # caller streams matrices through the library); the timed region covers all of it.
     e2e = None
     if not args.no_e2e:
         hA = torch.empty((m, stride), dtype=torch.int64, pin_memory=True)
         hA.copy_(A0.cpu())
-        hOut1 = torch.empty_like(hA, pin_memory=True)
-        hOut2 = torch.empty_like(hA, pin_memory=True) if with_rref else None
-        hP = torch.empty(m, dtype=torch.int64, pin_memory=True)
-        hQ = torch.empty(n, dtype=torch.int64, pin_memory=True)
-        hpiv = torch.empty(n, dtype=torch.int64, pin_memory=True)
-        hr = torch.empty(2, dtype=torch.int64, pin_memory=True)
+        comp = torch.cuda.current_stream(dev)
+        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        sets = []
+        for k in range(2):
+            sets.append({
+                "A": A1 if k == 0 else torch.empty_like(A0),
+                "A2": (A2 if k == 0 else torch.empty_like(A0)) if with_rref else None,
+                "P": P if k == 0 else torch.empty_like(P), "Q": Q if k == 0 else torch.empty_like(Q),
+                "r1": r1 if k == 0 else torch.empty_like(r1), "r2": r2 if k == 0 else torch.empty_like(r2),
+                "piv": piv if k == 0 else torch.empty_like(piv),
+                "hOut1": torch.empty_like(hA, pin_memory=True),
+                "hOut2": torch.empty_like(hA, pin_memory=True) if with_rref else None,
+                "hP": torch.empty(m, dtype=torch.int64, pin_memory=True),
+                "hQ": torch.empty(n, dtype=torch.int64, pin_memory=True),
+                "hpiv": torch.empty(n, dtype=torch.int64, pin_memory=True),
+                "hr": torch.empty(2, dtype=torch.int64, pin_memory=True),
+                "ev_in": torch.cuda.Event(), "ev_done": torch.cuda.Event(), "ev_out": torch.cuda.Event()})
+        for d in sets:
+            d["ev_out"].record(s_out)
 
-        def e2e_step():
-            A1.copy_(hA, non_blocking=True)
+        def e2e_step(i):
+            d = sets[i & 1]
+            with torch.cuda.stream(s_in):
+                s_in.wait_event(d["ev_out"])  # this set's previous results are out
+                d["A"].copy_(hA, non_blocking=True)
+                d["ev_in"].record(s_in)
+            comp.wait_event(d["ev_in"])
             if with_rref:
-                A2.copy_(A1)
-            step()
-            hOut1.copy_(A1, non_blocking=True)
-            hP.copy_(P, non_blocking=True)
-            hQ.copy_(Q, non_blocking=True)
-            hr[0:1].copy_(r1, non_blocking=True)
+                d["A2"].copy_(d["A"])
+            gf2.pls(d["A"], n, P=d["P"], Q=d["Q"], rank=d["r1"], work=wp, opts=opts)
             if with_rref:
-                hOut2.copy_(A2, non_blocking=True)
-                hpiv.copy_(piv, non_blocking=True)
-                hr[1:2].copy_(r2, non_blocking=True)
+                gf2.rref(d["A2"], n, rank=d["r2"], pivots=d["piv"], work=wr, opts=opts)
+            d["ev_done"].record(comp)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(d["ev_done"])
+                d["hOut1"].copy_(d["A"], non_blocking=True)
+                d["hP"].copy_(d["P"], non_blocking=True)
+                d["hQ"].copy_(d["Q"], non_blocking=True)
+                d["hr"][0:1].copy_(d["r1"], non_blocking=True)
+                if with_rref:
+                    d["hOut2"].copy_(d["A2"], non_blocking=True)
+                    d["hpiv"].copy_(d["piv"], non_blocking=True)
+                    d["hr"][1:2].copy_(d["r2"], non_blocking=True)
+                d["ev_out"].record(s_out)
 
-        e2e_step()
+        for i in range(2):  # warm-up: both buffer sets (first calls, graph captures)
+            e2e_step(i)
         torch.cuda.synchronize()
         e2e_steps = max(3, min(args.steps, 10))
         es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if world > 1:
             dist.barrier()
-        es.record()
-        for _ in range(e2e_steps):
-            e2e_step()
-        ee.record()
+        es.record(comp)
+        s_in.wait_event(es)
+        s_out.wait_event(es)
+        for i in range(e2e_steps):
+            e2e_step(i)
+        comp.wait_stream(s_out)
+        ee.record(comp)
         torch.cuda.synchronize()
         te_ms = max_over_ranks(es.elapsed_time(ee) / e2e_steps, world, dev)
+        last = sets[(e2e_steps - 1) & 1]
+        assert int(last["hr"][0].item()) == int(r1.item())  # the results did come back
         bi = m * stride * 8
         bo = m * stride * 8 + (m + n + 1) * 8 + ((m * stride * 8 + n * 8 + 8) if with_rref else 0)
         e2e = {"value": job_seconds_per_matrix(te_ms, world), "unit": "s", "h2d_bytes_per_step": bi,
-               "d2h_bytes_per_step": bo, "ms_per_step": te_ms, "steps": e2e_steps}
+               "d2h_bytes_per_step": bo, "ms_per_step": te_ms, "steps": e2e_steps,
+               "note": "two buffer sets: step i + 1's input copy and step i - 1's result copy overlap "
+                       "step i's elimination; all inside the timed region"}
 
     side = None
     if args.config == 3 and not args.no_side:

@@ -370,6 +370,8 @@ struct FrontSmem {
     u64 Ob[3][64];       // panel b's pivot rows at words b + 1, b + 2, b + 3
     u64 Oc[3][64];       // panel c's pivot rows: word b (raw), then words b + 2, b + 3 after panel b
     u64 zmb[64], zmc[64];  // the panels' zmaps
+    u64 ztc[64];           // panel c's pivot rows: coordinates over panel b's pivot rows
+    int prb[64], prc[64];  // physical rows of the pivots
     // 4-bit tables (16 positions x 16 values) of the sums of rows of Xb, Ob[0..2], zmb, Xc, Oc[1..2]
     u64 nib[8][256];
     int sc_[6];          // r_cur, kbar of panel b, kbar of panel c, window and swaps of b and c
@@ -410,6 +412,32 @@ __device__ __forceinline__ void build_nib(u64 *__restrict__ nib, const u64 *__re
     nib[e] = a;
 }
 
+// byte tables of maps [m0, m1): a warp per (map, byte position); lane l writes entries l + 32 k,
+// whose low nibble (l & 15) is fixed and whose high nibble is (l >> 4) + 2 k, so consecutive lanes
+// store consecutive entries (no bank conflict)
+__device__ __forceinline__ void build_bytetabs(FrontSmem &S, int m0, int m1)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int pq = warp; pq < (m1 - m0) * 8; pq += NT / 32) {
+        const int mp = m0 + (pq >> 3), q = pq & 7;
+        const u64 *im = S.img[mp] + 8 * q;
+        u64 lo = 0;
+#pragma unroll
+        for (int bit = 0; bit < 4; ++bit)
+            lo ^= ((lane >> bit) & 1) ? im[bit] : 0ull;
+        u64 *dst = S.tab[mp] + q * 256 + lane;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int hn = (lane >> 4) + 2 * k;
+            u64 hi = 0;
+#pragma unroll
+            for (int bit = 0; bit < 4; ++bit)
+                hi ^= ((hn >> bit) & 1) ? im[4 + bit] : 0ull;
+            dst[32 * k] = lo ^ hi;
+        }
+    }
+}
+
 // Physical row at trailing position p >= R2 of a pair: panel c's order, else panel b's, else perm
 // (the positions panel b changed are read through sb: this kernel writes them into perm).
 __device__ __forceinline__ int pair_row(const int *__restrict__ perm, const PanelState *__restrict__ sb,
@@ -431,6 +459,9 @@ __device__ __forceinline__ int pair_row(const int *__restrict__ perm, const Pane
     return perm[p];
 }
 
+// The work is ordered so that everything before the marked point reads only this pair's pivot
+// search results and the words b, b + 1 that the previous front wrote; the words b + 2, b + 3 of
+// the rows (the previous sweep's) and every write come after it.
 __global__ void __launch_bounds__(NT, 1)
 k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, const PanelState *__restrict__ sb,
              const PanelState *__restrict__ sc, u64 *__restrict__ zb, u64 *__restrict__ zc,
@@ -455,117 +486,121 @@ k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, c
     // consecutive positions go to different CTAs, so the pivot rows (the first positions, whose
     // rows cost most here) spread over the grid
     const int g = tid * gridDim.x + blockIdx.x, gs = gridDim.x * NT;
-    // panel b's row order into perm (its pivot search of panel c left it out)
+    // a CTA past the last row only takes its share of the row-order update below
+    const bool rows = R0 + (int)blockIdx.x < m;
+    const bool pivots = rows && (kb > 0 || kc > 0);
+    // ---- before the wait: the maps of words b and b + 1 ----
+    int p = R0 + g, ph = -1;
+    u64 w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+    if (pivots && p >= R1 && p < m) {
+        ph = p < R2 ? sc->prow[p - R1] : pair_row(perm, sb, sc, R0, R1, nwb, nxb, nwc, nxc, p);
+        const ulonglong2 lo = *reinterpret_cast<const ulonglong2 *>(Fc + 4 * (int64_t)ph);
+        w0 = lo.x;
+        w1 = lo.y;
+    }
+    if (pivots) {
+        if (tid < 64) {
+            const int t = tid;
+            S.prb[t] = t < kb ? sb->prow[t] : 0;
+            S.prc[t] = t < kc ? sc->prow[t] : 0;
+            S.Xb[t] = t < kb ? sb->newblk[t] & sb->J & lowmask(sb->pcol[t] + 1) : 0ull;
+            S.Ob[0][t] = t < kb && has1 ? Fc[4 * (int64_t)S.prb[t] + 1] : 0ull;
+            S.Xc[t] = t < kc ? sc->newblk[t] & sc->J & lowmask(sc->pcol[t] + 1) : 0ull;
+            S.Oc[0][t] = t < kc ? Fc[4 * (int64_t)S.prc[t]] : 0ull;
+        }
+        __syncthreads();
+        for (int e = tid; e < 4 * 256; e += NT) {
+            const int k = e >> 8;  // Xb, Ob0, zmb, Xc
+            const int slot = k == 0 ? N_XB : k == 1 ? N_OB0 : k == 2 ? N_ZMB : N_XC;
+            const u64 *src = k == 0 ? S.Xb : k == 1 ? S.Ob[0] : k == 2 ? S.zmb : S.Xc;
+            build_nib(S.nib[slot], src, e & 255);
+        }
+        __syncthreads();
+        if (tid < 3 * 64) {
+            // panel b's maps of word b: z_b, multipliers, contribution to word b + 1
+            const int mp = tid >> 6, i = tid & 63;
+            const u64 zm = S.zmb[i];
+            S.img[mp][i] = mp == 0 ? zm : select_sum(zm, S.nib[mp == 1 ? N_XB : N_OB0]);
+        } else if (tid < 5 * 64) {
+            // panel c's maps of word b + 1 after panel b: z_c, multipliers
+            const int mp = (tid >> 6) - 3, i = tid & 63;
+            const u64 zm = S.zmc[i];
+            S.img[M_ZC + mp][i] = mp == 0 ? zm : select_sum(zm, S.nib[N_XC]);
+        } else if (tid < 6 * 64) {
+            // panel c's pivot rows: their coordinates over panel b's pivot rows
+            const int t = tid - 5 * 64;
+            S.ztc[t] = t < kc ? select_sum(S.Oc[0][t], S.nib[N_ZMB]) : 0ull;
+        }
+        __syncthreads();
+        build_bytetabs(S, M_ZB, M_CB + 1);
+        build_bytetabs(S, M_ZC, M_XC + 1);
+    }
+    // ---- then: panel b's row order, the words b + 2, b + 3 and every write ----
     if (sc) {
         for (int i = g; i < nwb; i += gs)
             perm[R0 + i] = sb->wperm[i];
         for (int x = g; x < nxb; x += gs)
             perm[sb->xpos[x]] = sb->xval[x];
     }
-    if (R0 + (int)blockIdx.x >= m)
+    if (!rows)
         return;
-    if (kb == 0 && kc == 0) {
+    if (!pivots) {
         // no pivot: words b, b + 1 of every row below are zero; words b + 2, b + 3 pass to the next
         // pair unchanged (zero too once the tail is known to be zero)
         const bool zt = sb->zero_tail;
-        for (int p = R0 + g; p < m; p += gs) {
-            const int ph = pair_row(perm, sb, sc, R0, R1, nwb, nxb, nwc, nxc, p);
-            uint64_t *row = A + (int64_t)ph * stride + b;
+        for (int q = R0 + g; q < m; q += gs) {
+            const int r = pair_row(perm, sb, sc, R0, R1, nwb, nxb, nwc, nxc, q);
+            uint64_t *row = A + (int64_t)r * stride + b;
             row[0] = 0ull;
             if (sc)
                 row[1] = 0ull;
             if (sc && has2) {
-                Fn[4 * (int64_t)ph] = zt ? 0ull : Fc[4 * (int64_t)ph + 2];
+                Fn[4 * (int64_t)r] = zt ? 0ull : Fc[4 * (int64_t)r + 2];
                 if (has3)
-                    Fn[4 * (int64_t)ph + 1] = zt ? 0ull : Fc[4 * (int64_t)ph + 3];
+                    Fn[4 * (int64_t)r + 1] = zt ? 0ull : Fc[4 * (int64_t)r + 3];
             }
         }
         return;
     }
-    // this thread's first row: its words are loaded while the tables are built
-    int p = R0 + g, ph = -1;
-    u64 w0 = 0, w1 = 0, w2 = 0, w3 = 0;
-    if (p >= R1 && p < m) {
-        ph = p < R2 ? sc->prow[p - R1] : pair_row(perm, sb, sc, R0, R1, nwb, nxb, nwc, nxc, p);
-        const ulonglong2 *f = reinterpret_cast<const ulonglong2 *>(Fc + 4 * (int64_t)ph);
-        const ulonglong2 lo = f[0];
-        w0 = lo.x;
-        w1 = lo.y;
-        if (p >= R2) {
-            const ulonglong2 hi = f[1];
-            w2 = hi.x;
-            w3 = hi.y;
-        }
+    if (ph >= 0 && p >= R2) {
+        const ulonglong2 hi = *reinterpret_cast<const ulonglong2 *>(Fc + 4 * (int64_t)ph + 2);
+        w2 = hi.x;
+        w3 = hi.y;
     }
     if (tid < 64) {
         const int t = tid;
-        const u64 *rb = Fc + 4 * (int64_t)(t < kb ? sb->prow[t] : 0);
-        const u64 *rc = Fc + 4 * (int64_t)(t < kc ? sc->prow[t] : 0);
-        S.Xb[t] = t < kb ? sb->newblk[t] & sb->J & lowmask(sb->pcol[t] + 1) : 0ull;
-        S.Ob[0][t] = t < kb && has1 ? rb[1] : 0ull;
-        S.Ob[1][t] = t < kb && has2 ? rb[2] : 0ull;
-        S.Ob[2][t] = t < kb && has3 ? rb[3] : 0ull;
-        S.Xc[t] = t < kc ? sc->newblk[t] & sc->J & lowmask(sc->pcol[t] + 1) : 0ull;
-        S.Oc[0][t] = t < kc ? rc[0] : 0ull;
-        S.Oc[1][t] = t < kc && has2 ? rc[2] : 0ull;
-        S.Oc[2][t] = t < kc && has3 ? rc[3] : 0ull;
+        S.Ob[1][t] = t < kb && has2 ? Fc[4 * (int64_t)S.prb[t] + 2] : 0ull;
+        S.Ob[2][t] = t < kb && has3 ? Fc[4 * (int64_t)S.prb[t] + 3] : 0ull;
+        S.Oc[1][t] = t < kc && has2 ? Fc[4 * (int64_t)S.prc[t] + 2] : 0ull;
+        S.Oc[2][t] = t < kc && has3 ? Fc[4 * (int64_t)S.prc[t] + 3] : 0ull;
     }
     __syncthreads();
-    for (int e = tid; e < 6 * 256; e += NT) {
-        const int k = e >> 8;
-        const u64 *src = k == N_XB ? S.Xb : k == N_ZMB ? S.zmb : k == N_XC ? S.Xc : S.Ob[k - N_OB0];
-        build_nib(S.nib[k], src, e & 255);
-    }
+    for (int e = tid; e < 2 * 256; e += NT)
+        build_nib(S.nib[N_OB1 + (e >> 8)], S.Ob[1 + (e >> 8)], e & 255);
     __syncthreads();
-    if (tid < 5 * 64) {
-        // panel b's maps: bit i of word b -> ...
+    if (tid < 2 * 64) {
+        // panel b's contributions to words b + 2, b + 3
         const int mp = tid >> 6, i = tid & 63;
-        const u64 zm = S.zmb[i];
-        S.img[mp][i] = mp == 0 ? zm : select_sum(zm, S.nib[mp == 1 ? N_XB : N_OB0 + mp - 2]);
-    } else if (tid < 5 * 64 + 64) {
-        // panel c's pivot rows at words b + 2, b + 3 after panel b (their coordinates over O_b
-        // from their word b)
-        const int t = tid - 5 * 64;
+        S.img[M_E2B + mp][i] = select_sum(S.zmb[i], S.nib[N_OB1 + mp]);
+    } else if (tid < 3 * 64) {
+        // panel c's pivot rows at words b + 2, b + 3 after panel b
+        const int t = tid - 2 * 64;
         if (t < kc) {
-            const u64 zt = select_sum(S.Oc[0][t], S.nib[N_ZMB]);
-            S.Oc[1][t] ^= select_sum(zt, S.nib[N_OB1]);
-            S.Oc[2][t] ^= select_sum(zt, S.nib[N_OB2]);
+            S.Oc[1][t] ^= select_sum(S.ztc[t], S.nib[N_OB1]);
+            S.Oc[2][t] ^= select_sum(S.ztc[t], S.nib[N_OB2]);
         }
     }
     __syncthreads();
     for (int e = tid; e < 2 * 256; e += NT)
         build_nib(S.nib[N_OC1 + (e >> 8)], S.Oc[1 + (e >> 8)], e & 255);
     __syncthreads();
-    if (tid < 4 * 64) {
+    if (tid < 2 * 64) {
         const int mp = tid >> 6, i = tid & 63;
-        const u64 zm = S.zmc[i];
-        S.img[M_ZC + mp][i] = mp == 0 ? zm : select_sum(zm, S.nib[mp == 1 ? N_XC : N_OC1 + mp - 2]);
+        S.img[M_E2C + mp][i] = select_sum(S.zmc[i], S.nib[N_OC1 + mp]);
     }
     __syncthreads();
-    {
-        // a warp per (map, byte position): lane l writes entries l + 32 k, whose low nibble
-        // (l & 15) is fixed and whose high nibble is (l >> 4) + 2 k: consecutive lanes store
-        // consecutive entries (no bank conflict)
-        const int warp = tid >> 5, lane = tid & 31;
-        for (int pq = warp; pq < NMAP * 8; pq += NT / 32) {
-            const int mp = pq >> 3, q = pq & 7;
-            const u64 *im = S.img[mp] + 8 * q;
-            u64 lo = 0;
-#pragma unroll
-            for (int bit = 0; bit < 4; ++bit)
-                lo ^= ((lane >> bit) & 1) ? im[bit] : 0ull;
-            u64 *dst = S.tab[mp] + q * 256 + lane;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int hn = (lane >> 4) + 2 * k;
-                u64 hi = 0;
-#pragma unroll
-                for (int bit = 0; bit < 4; ++bit)
-                    hi ^= ((hn >> bit) & 1) ? im[4 + bit] : 0ull;
-                dst[32 * k] = lo ^ hi;
-            }
-        }
-    }
+    build_bytetabs(S, M_E2B, M_E3B + 1);
+    build_bytetabs(S, M_E2C, M_E3C + 1);
     __syncthreads();
     for (; p < m; p += gs) {
         if (ph < 0 && p >= R1) {
@@ -709,9 +744,9 @@ static int pair_front(const Elim &e, int b, bool has_c, cudaStream_t s)
     const int64_t need = (e.m + NT - 1) / NT;
     const int grid = (int)(need < nsm ? (need > 0 ? need : 1) : nsm);
     const int tok = prof_begin(s);
-    k_pair_front<<<grid, NT, FRONT_SMEM, s>>>(e.A, e.stride, e.perm, e.st + (b & 3), has_c ? e.st + ((b + 1) & 3) : nullptr,
-                                              pair_zb(e), pair_zc(e), pair_F(e, b), pair_F(e, b + 2), e.out, e.ostride,
-                                              (int)e.m, (int)e.W, b);
+    k_pair_front<<<grid, NT, FRONT_SMEM, s>>>(e.A, e.stride, e.perm, e.st + (b & 3),
+                                              has_c ? e.st + ((b + 1) & 3) : nullptr, pair_zb(e), pair_zc(e),
+                                              pair_F(e, b), pair_F(e, b + 2), e.out, e.ostride, (int)e.m, (int)e.W, b);
     prof_end(s, GF2_PROF_COORDS, tok);
     prof_launched(1);
     return note_cuda(cudaGetLastError());
