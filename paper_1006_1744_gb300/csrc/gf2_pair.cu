@@ -16,7 +16,7 @@
 //     it writes the multipliers of L into words b and b + 1, both panels'
 //     updates into words b + 2 and b + 3 (the next pair's panel words), the
 //     pivot rows' final words b .. b + 3 into `out`, and panel b's row order into
-//     perm. Byte tables of the linear maps involved do all of it;
+//     perm. 4-bit tables of the linear maps involved do all of it;
 //   * k_pair_sweep: MakeTable1 for both panels on 8-word column tiles, O_c formed
 //     from O_b's tables, and row ^= z_b.O_b ^ z_c.O_c on every trailing row from
 //     word b + 4 on. One 128-byte line of shared memory holds entry v of both
@@ -352,8 +352,8 @@ __global__ void __launch_bounds__(NT, 1) k_pair_sweep(PairArgs a)
 
 // ---------------------------------------------------------------------------
 // The front of a pair: every row's coordinates, the multipliers of L in words b and b + 1, and
-// both panels' updates of words b + 2 and b + 3 (the next pair's panel words), all from byte
-// tables (8 byte positions x 256 values) of linear maps of a row's panel words:
+// both panels' updates of words b + 2 and b + 3 (the next pair's panel words), all from 4-bit
+// tables (16 positions x 16 values) of linear maps of a row's panel words:
 //   from word b:                   Zb -> z_b, Xb -> panel b's multipliers (z_b.X_b, X_t = pivot
 //                                  t's multipliers plus its own bit), Cb, E2b, E3b -> z_b.O_b at
 //                                  words b + 1, b + 2, b + 3;
@@ -364,7 +364,7 @@ constexpr int NMAP = 9;
 enum { M_ZB, M_XB, M_CB, M_E2B, M_E3B, M_ZC, M_XC, M_E2C, M_E3C };
 
 struct FrontSmem {
-    u64 tab[NMAP][8 * 256];
+    u64 tab[NMAP][256];  // 4-bit tables of the maps (16 positions x 16 values): one 128-byte bank row per position
     u64 img[NMAP][64];   // image of each bit of the panel word
     u64 Xb[64], Xc[64];
     u64 Ob[3][64];       // panel b's pivot rows at words b + 1, b + 2, b + 3
@@ -378,14 +378,6 @@ struct FrontSmem {
 };
 enum { N_XB, N_OB0, N_OB1, N_OB2, N_ZMB, N_XC, N_OC1, N_OC2 };
 
-__device__ __forceinline__ u64 bytesum(const u64 *__restrict__ t, u64 w)
-{
-    u64 a = 0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-        a ^= t[q * 256 + (int)((w >> (8 * q)) & 255u)];
-    return a;
-}
 
 // sum of the 64 rows src[0..63] selected by the set bits of z, through its 4-bit table (sixteen
 // lookups, two XOR chains)
@@ -400,6 +392,10 @@ __device__ __forceinline__ u64 select_sum(u64 z, const u64 *__restrict__ nib)
     return a0 ^ a1;
 }
 
+// the image of a panel word w under a linear map, through the map's 4-bit table: the sixteen
+// entries of a position fill one 128-byte row of banks, so every lookup is free of bank conflicts
+__device__ __forceinline__ u64 select_sum_w(const u64 *__restrict__ nib, u64 w) { return select_sum(w, nib); }
+
 // 4-bit tables of 64 rows: entry (q, v) = the sum of rows 4 q + j for the set bits j of v. Lane l
 // of a warp writes entries l and l + 32 of a table (consecutive lanes, consecutive entries).
 __device__ __forceinline__ void build_nib(u64 *__restrict__ nib, const u64 *__restrict__ src, int e)
@@ -412,30 +408,11 @@ __device__ __forceinline__ void build_nib(u64 *__restrict__ nib, const u64 *__re
     nib[e] = a;
 }
 
-// byte tables of maps [m0, m1): a warp per (map, byte position); lane l writes entries l + 32 k,
-// whose low nibble (l & 15) is fixed and whose high nibble is (l >> 4) + 2 k, so consecutive lanes
-// store consecutive entries (no bank conflict)
+// 4-bit tables of the maps [m0, m1), from their images of the 64 bits
 __device__ __forceinline__ void build_bytetabs(FrontSmem &S, int m0, int m1)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int pq = warp; pq < (m1 - m0) * 8; pq += NT / 32) {
-        const int mp = m0 + (pq >> 3), q = pq & 7;
-        const u64 *im = S.img[mp] + 8 * q;
-        u64 lo = 0;
-#pragma unroll
-        for (int bit = 0; bit < 4; ++bit)
-            lo ^= ((lane >> bit) & 1) ? im[bit] : 0ull;
-        u64 *dst = S.tab[mp] + q * 256 + lane;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int hn = (lane >> 4) + 2 * k;
-            u64 hi = 0;
-#pragma unroll
-            for (int bit = 0; bit < 4; ++bit)
-                hi ^= ((hn >> bit) & 1) ? im[4 + bit] : 0ull;
-            dst[32 * k] = lo ^ hi;
-        }
-    }
+    for (int e = threadIdx.x; e < (m1 - m0) * 256; e += NT)
+        build_nib(S.tab[m0 + (e >> 8)], S.img[m0 + (e >> 8)], e & 255);
 }
 
 // Physical row at trailing position p >= R2 of a pair: panel c's order, else panel b's, else perm
@@ -630,8 +607,8 @@ k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, c
             // pivot of panel c: panel b's multipliers in A, its final words b + 1 .. b + 3
             const int t = p - R1;
             uint64_t *row = A + (int64_t)ph * stride + b;
-            zb[ph] = bytesum(S.tab[M_ZB], w0);
-            row[0] = bytesum(S.tab[M_XB], w0);
+            zb[ph] = select_sum_w(S.tab[M_ZB], w0);
+            row[0] = select_sum_w(S.tab[M_XB], w0);
             if (out) {
                 uint64_t *o = out + (int64_t)p * ostride + b;
                 const u64 zt = sc->zpiv[t];
@@ -643,16 +620,16 @@ k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, c
             }
         } else {
             uint64_t *row = A + (int64_t)ph * stride + b;
-            const u64 zbv = bytesum(S.tab[M_ZB], w0);
-            u64 n2 = w2 ^ bytesum(S.tab[M_E2B], w0), n3 = w3 ^ bytesum(S.tab[M_E3B], w0);
-            row[0] = bytesum(S.tab[M_XB], w0);
+            const u64 zbv = select_sum_w(S.tab[M_ZB], w0);
+            u64 n2 = w2 ^ select_sum_w(S.tab[M_E2B], w0), n3 = w3 ^ select_sum_w(S.tab[M_E3B], w0);
+            row[0] = select_sum_w(S.tab[M_XB], w0);
             zb[ph] = zbv;
             if (sc) {
-                const u64 v1 = w1 ^ bytesum(S.tab[M_CB], w0);
-                zc[ph] = bytesum(S.tab[M_ZC], v1);
-                row[1] = bytesum(S.tab[M_XC], v1);
-                n2 ^= bytesum(S.tab[M_E2C], v1);
-                n3 ^= bytesum(S.tab[M_E3C], v1);
+                const u64 v1 = w1 ^ select_sum_w(S.tab[M_CB], w0);
+                zc[ph] = select_sum_w(S.tab[M_ZC], v1);
+                row[1] = select_sum_w(S.tab[M_XC], v1);
+                n2 ^= select_sum_w(S.tab[M_E2C], v1);
+                n3 ^= select_sum_w(S.tab[M_E3C], v1);
             }
             // words b + 2, b + 3 after both panels: the next pair's panel words, read by its pivot
             // searches and its front from here (A gets them as multipliers then)
