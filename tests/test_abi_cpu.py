@@ -170,3 +170,29 @@ def test_mul_workspace_bytes_by_product_form():
     assert gf2.mul_workspace_bytes(4096, 4096, 4096, {"product": 4, "cutoff_cols": 1024}) > two
     assert gf2.mul_workspace_bytes(-1, 4, 4, None) == 0
     assert gf2.mul_workspace_bytes(64, 64, 64, {"product": 5}) == 0
+
+
+def test_panels_per_sweep_option_host_only(built):
+    """panels_per_sweep: 0 (the library's choice), 1 or 2; other values are refused before any
+    device work, and two panels per sweep size the workspace for the coordinates of every row over
+    both panels' pivot rows and two buffers of four panel words per row (8 more words per row)."""
+    from paper_1006_1744_gb300 import gf2
+    m, n = 1000, 3000
+    one = gf2.workspace_bytes(gf2.OP_PLS, m, n, {"panels_per_sweep": 1})
+    two = gf2.workspace_bytes(gf2.OP_PLS, m, n, {"panels_per_sweep": 2})
+    assert one > 0 and two >= one + 8 * 8 * m and two <= one + 8 * 8 * m + 512
+    assert gf2.workspace_bytes(gf2.OP_PLS, m, n) == one  # small: one panel per sweep by default
+    big = 30000
+    assert gf2.workspace_bytes(gf2.OP_RANK, big, big) == gf2.workspace_bytes(gf2.OP_RANK, big, big,
+                                                                             {"panels_per_sweep": 2})
+    # the reduced-form routes of gf2_rref sweep one panel at a time whatever the option says
+    assert gf2.workspace_bytes(gf2.OP_RREF, m, n, {"panels_per_sweep": 2, "rref_method": gf2.RREF_M4RI}) == \
+        gf2.workspace_bytes(gf2.OP_RREF, m, n, {"panels_per_sweep": 1, "rref_method": gf2.RREF_M4RI})
+    for bad in (-1, 3, 64):
+        assert gf2.workspace_bytes(gf2.OP_PLS, m, n, {"panels_per_sweep": bad}) == 0
+    L = gf2.lib()
+    o = gf2.Opts()
+    o.panels_per_sweep = 3
+    fake = ctypes.c_void_p(1 << 20)
+    P = Q = rank = ctypes.c_void_p(1 << 21)
+    assert L.gf2_pls(fake, 8, 8, 16, P, Q, rank, None, 0, ctypes.byref(o), None) == 1  # GF2_EINVAL
