@@ -36,14 +36,16 @@ int64_t min_stride(int64_t n)
     return s < 16 ? 16 : s;
 }
 
-// Two panels per sweep once the trailing block's sweeps outweigh the serial pivot searches
-// (measured on GB300: 32768^2 15.3 against 16.7 ms, 65536^2 75 against 92 ms; 16384^2 6.1 against
-// 4.9 ms, where the pivot chain sets the time)
+// Two panels per sweep once the trailing block's sweeps outweigh the serial pivot searches: a
+// panel's sweep grows with rows x words, the pivot search does not (measured on GB300, one panel
+// per sweep against two: 20480^2 6.79 / 6.94 ms, 24576^2 9.33 / 9.09, 16384 x 65536 12.10 / 11.58,
+// 65536 x 16384 10.37 / 8.73, 65536^2 92 / 74; 16384^2 4.9 / 6.1, where the pivot chain sets the time)
 int pps_choice(const gf2_opts *o, int64_t m, int64_t n)
 {
     if (o && o->panels_per_sweep)
         return o->panels_per_sweep;
-    return m >= 24576 && n >= 24576 ? 2 : 1;
+    const int64_t W = (n + 63) / 64;
+    return m >= 16384 && m * W >= (int64_t)8 << 20 ? 2 : 1;
 }
 
 // gf2_rref: the PLS route takes the panels per sweep of the PLS form; the reduced-form routes
