@@ -6,10 +6,11 @@
 // both (AddRowsFromTable of Sec. 3.1 / 4.1 over 128 pivot columns), which halves
 // the DRAM traffic of the sweeps and keeps their shared-memory lookups per panel
 // the same:
-//   * k_pivot_pair (gf2_pls.cu): the pivots of panel b (A's word b is current),
-//     then of panel c = b + 1 (A's word b + 1 plus panel b's contribution, the
-//     look-ahead of the one-panel pipeline), panel b's row order left out of
-//     perm while the previous sweep still reads it;
+//   * k_pivot_pair (gf2_pls.cu): the pivots of panel b, then of panel c = b + 1
+//     (word b + 1 plus panel b's contribution, the look-ahead of the one-panel
+//     pipeline), reading the rows' words from F, a contiguous buffer of words
+//     b .. b + 3 of every row; panel b's row order is left out of perm while
+//     the previous sweep still reads it;
 //   * k_pair_front: the coordinates z_b of every row below panel b's pivots over
 //     panel b's pivot rows O_b, and z_c of every row below both panels' pivots
 //     over O_c (panel c's pivot rows after panel b), from its words b and b + 1;
