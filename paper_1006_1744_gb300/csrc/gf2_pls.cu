@@ -1449,10 +1449,10 @@ __global__ void k_copyback_b(const gf2::ElimDesc *__restrict__ D)
 // ---------------------------------------------------------------------------
 // Batched elimination in one persistent launch (cooperative: every CTA is
 // resident). Teams of G CTAs eliminate one matrix at a time, panel by panel:
-// the pivot search of panel b (the first PIVOT_THREADS threads of the team's
-// first CTA), then the table sweep of panel b over all of the team's CTAs,
-// with a team barrier after each, then the finishing steps (row order, gather,
-// compression of L, copy back). The large matrices go to teams of CTAs (a
+// the pivot search of panel b + 1 (the first PIVOT_THREADS threads of the
+// team's first CTA) beside the table sweep of panel b (the other threads of all
+// of the team's CTAs), with a team barrier after each step, then the finishing
+// steps (row order, gather, compression of L, copy back). The large matrices go to teams of CTAs (a
 // contiguous CTA range and a list of matrices per team, planned on the host);
 // every CTA then takes small matrices one at a time from a device work queue,
 // as a team of one.
@@ -1532,14 +1532,29 @@ __device__ bool team_eliminate(SweepSmem &S, const gf2::ElimDesc &d, int tr, int
     }
     if (!team_barrier(bar, target, G, pl))
         return false;
+    // pivot search of panel c by the first PIVOT_THREADS threads of the team's first CTA
+    auto search = [&](int c) {
+        pivot_panel(d.A + c, d.stride, d.side + (size_t)((c + 1) & 1) * m, 1, d.perm, d.st + ((c + 1) & 1),
+                    d.st + (c & 1), d.P, d.Q, m, c, min(64, d.n - 64 * c), 0, 0);
+    };
+    if (W > 0 && tr == 0 && tid < PIVOT_THREADS)
+        search(0);
+    if (!team_barrier(bar, target, G, pl))
+        return false;
     for (int b = 0; b < W; ++b) {
-        if (tr == 0 && tid < PIVOT_THREADS)
-            pivot_panel(d.A + b, d.stride, d.side + (size_t)((b + 1) & 1) * m, 1, d.perm, d.st + ((b + 1) & 1),
-                        d.st + (b & 1), d.P, d.Q, m, b, min(64, d.n - 64 * b), 0, 0);
-        if (!team_barrier(bar, target, G, pl))
-            return false;
-        sweep_panel16<0, 8>(S, d.A, d.stride, d.side + (size_t)(b & 1) * m, d.side + (size_t)((b + 1) & 1) * m, d.perm,
-                         d.st + (b & 1), d.out, d.ostride, nullptr, m, W, b, tr, G);
+        // The search of panel b + 1 runs beside the sweep of panel b (the other warps of every CTA
+        // of the team), as the two kernels do in the one-matrix elimination: it forms its window's
+        // words from A's word b + 1, which this sweep leaves as it is, and panel b's coordinates
+        // in the side buffer, which this sweep only reads; the rows whose order panel b changed
+        // are read by the sweep from panel b's state, not from perm.
+        if (tid < PIVOT_THREADS) {
+            if (tr == 0 && b + 1 < W)
+                search(b + 1);
+        } else {
+            sweep_panel16<0, 8, NT - PIVOT_THREADS, PIVOT_THREADS>(
+                S, d.A, d.stride, d.side + (size_t)(b & 1) * m, d.side + (size_t)((b + 1) & 1) * m, d.perm,
+                d.st + (b & 1), d.out, d.ostride, nullptr, m, W, b, tr, G);
+        }
         if (!team_barrier(bar, target, G, pl))
             return false;
     }

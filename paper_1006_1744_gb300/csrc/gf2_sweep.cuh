@@ -13,6 +13,31 @@ constexpr int NT = 512;        // threads per CTA
 constexpr int TPR = 4;         // threads per row, four words each
 constexpr int RPU = NT / TPR;  // rows per block (128)
 
+// The sweep runs on NTH threads starting at thread TOFF of the CTA: the whole CTA (NTH = NT,
+// TOFF = 0, CTA barriers) or, in the persistent batched elimination, the warps after the pivot
+// search's, which synchronise on named barrier 2 of their own.
+template <int NTH, int TOFF>
+__device__ __forceinline__ void sweep_sync()
+{
+    if (NTH == NT && TOFF == 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync 2, %0;" ::"n"(NTH) : "memory");
+}
+
+template <int NTH, int TOFF>
+__device__ __forceinline__ bool sweep_sync_or(bool v)
+{
+    if (NTH == NT && TOFF == 0)
+        return __syncthreads_or(v) != 0;
+    unsigned r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 2, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+                 : "=r"(r)
+                 : "r"((unsigned)v), "n"(NTH)
+                 : "memory");
+    return r != 0;
+}
+
 struct SweepSmem {
     u64 T[8 * 128 * TW];  // half tables: group g, entry v < 128 at (g * 128 + v) * TW
     u64 U[256 * TW];      // sums of the rows 8 g + 7 selected by the 8 top bits
@@ -153,7 +178,7 @@ __device__ __forceinline__ void prefetch_l2(const void *p)
 // holds the panel word b, word b + 1 or words past W, so threads with such words store per word.
 // Pipeline: physical row 5 blocks ahead, an L2 prefetch of the row's 128-byte line 4 ahead, the
 // panel word 3 ahead, the row data 2 ahead (registers), then the block itself.
-template <int MODE, bool UP, bool EDGE, bool COUNT, int KB>
+template <int MODE, bool UP, bool EDGE, bool COUNT, int KB, int RP = RPU>
 __device__ __forceinline__ void lean_blocks(const Cfg &c, const SweepSmem &S, const Lanes &L, int w0, int ja, int jb,
                                             unsigned long long &cnt)
 {
@@ -169,7 +194,7 @@ __device__ __forceinline__ void lean_blocks(const Cfg &c, const SweepSmem &S, co
     u64 d0[4] = {0, 0, 0, 0}, d1[4] = {0, 0, 0, 0}, d2[4] = {0, 0, 0, 0};
     // positions clamped into [0, m): the loads of the pipeline's first and last iterations (blocks
     // before ja or past the range or the matrix) read valid rows and are never used
-    auto pos = [&](int jj) { return min(max(pbase + jj * RPU, 0), plast); };
+    auto pos = [&](int jj) { return min(max(pbase + jj * RP, 0), plast); };
     for (int j = ja - 5; j < jb; ++j) {
         if (!UP) {
             ph5 = c.perm[pos(j + 5)];
@@ -199,7 +224,7 @@ __device__ __forceinline__ void lean_blocks(const Cfg &c, const SweepSmem &S, co
             }
         }
         if (j >= ja) {
-            const int p = pbase + j * RPU;
+            const int p = pbase + j * RP;
             const u64 z = coords(S, L, wv0);
             u64 x[4];
             lookup<KB>(L, z, x);
@@ -266,11 +291,11 @@ __device__ __forceinline__ int row_code(const Cfg &c, int p)
 }
 
 // One block of any tile, any rows (pivot rows, window rows, the panel word's tile).
-template <int MODE, bool COUNT, int KB>
+template <int MODE, bool COUNT, int KB, int RP = RPU>
 __device__ __forceinline__ void general_block(const Cfg &c, const SweepSmem &S, const Lanes &L, int w0, int j,
                                               unsigned long long &cnt)
 {
-    const int p = c.row0 + j * RPU + L.rg;
+    const int p = c.row0 + j * RP + L.rg;
     const int code = row_code(c, p);
     u64 wv = 0;
     if (code >= 0)
@@ -321,11 +346,12 @@ __device__ __forceinline__ void general_block(const Cfg &c, const SweepSmem &S, 
 }
 
 // The sweep proper (the panel has pivots): tables per tile, then the blocks of each tile.
-template <int MODE, bool COUNT, int KB>
+template <int MODE, bool COUNT, int KB, int NTH = NT, int TOFF = 0>
 __device__ __forceinline__ void sweep_body(Cfg &c, SweepSmem &S, unsigned long long &cnt, int cta, int ncta)
 {
+    constexpr int RP = NTH / TPR;  // rows per block
     c.row0 = MODE ? 0 : c.r;
-    const int tid = threadIdx.x;
+    const int tid = (int)threadIdx.x - TOFF;
     const int m = c.m, W = c.W, b = c.b;
     const int64_t stride = c.stride;
     const uint64_t *__restrict__ A = c.A;
@@ -336,22 +362,22 @@ __device__ __forceinline__ void sweep_body(Cfg &c, SweepSmem &S, unsigned long l
         return;
     const int wstart = b & ~(TW - 1);
     const int tiles = (W - wstart + TW - 1) / TW;
-    const int nblk = (M + RPU - 1) / RPU;
+    const int nblk = (M + RP - 1) / RP;
     const long long total = (long long)tiles * nblk;
     const long long q_lo = total * cta / ncta, q_hi = total * (cta + 1) / ncta;
     if (q_lo >= q_hi)
         return;
     // blocks [0, up_end) hold only rows above the panel (MODE 1); blocks from plain_blk on hold
     // only trailing rows that perm alone gives; the blocks between take the general path
-    const int up_end = MODE ? (c.r - c.row0) / RPU : 0;
+    const int up_end = MODE ? (c.r - c.row0) / RP : 0;
     const int plain_from = c.nx ? INT_MAX : c.r + max(c.kbar, c.nwin);
-    const int plain_blk = c.nx ? nblk : min(nblk, (plain_from - c.row0 + RPU - 1) / RPU);
+    const int plain_blk = c.nx ? nblk : min(nblk, (plain_from - c.row0 + RP - 1) / RP);
 
     if (tid < 64) {
         S.map[tid] = st->zmap[tid];
         S.prow[tid] = tid < c.kbar ? st->prow[tid] : 0;
     }
-    __syncthreads();
+    sweep_sync<NTH, TOFF>();
     if (tid < 8 * 16) {
         // coordinate table of byte position q, entries (vh << 4) | low in Gray-code order of the
         // low nibble (one XOR per entry), both copies
@@ -385,8 +411,8 @@ __device__ __forceinline__ void sweep_body(Cfg &c, SweepSmem &S, unsigned long l
         q = q_end;
         const int wbase = wstart + tile * TW;
         // ---- tables of this tile (MakeTable over the rows of O, Gray-code order) ----
-        __syncthreads();
-        for (int e = tid; e < 64 * TW; e += NT) {
+        sweep_sync<NTH, TOFF>();
+        for (int e = tid; e < 64 * TW; e += NTH) {
             const int t = e / TW, w = wbase + e % TW;
             u64 v = 0;
             if (t < c.kbar && w < W && w >= b) {
@@ -400,17 +426,17 @@ __device__ __forceinline__ void sweep_body(Cfg &c, SweepSmem &S, unsigned long l
             }
             S.O[e] = v;
         }
-        __syncthreads();
+        sweep_sync<NTH, TOFF>();
         if (KB == 4) {
             // 16 tables of the 16 sums of 4 pivot rows each
-            for (int e = tid; e < 16 * TW; e += NT) {
+            for (int e = tid; e < 16 * TW; e += NTH) {
                 const int wi = e % TW, g = e / TW;
                 const u64 *Og = S.O + (4 * g) * TW + wi;
                 gray16(0ull, Og[0], Og[TW], Og[2 * TW], Og[3 * TW], S.T + (g * 16) * TW + wi, TW);
             }
-            __syncthreads();
+            sweep_sync<NTH, TOFF>();
         } else {
-            for (int e = tid; e < 8 * 8 * TW; e += NT) {
+            for (int e = tid; e < 8 * 8 * TW; e += NTH) {
                 // group g, high bits vh (rows 8 g + 4 .. 8 g + 6), word wi: 16 entries by Gray code
                 const int wi = e % TW, vh = (e / TW) & 7, g = e / (8 * TW);
                 const u64 *Og = S.O + (8 * g) * TW + wi;
@@ -429,25 +455,25 @@ __device__ __forceinline__ void sweep_body(Cfg &c, SweepSmem &S, unsigned long l
                     base ^= ((vh >> bit) & 1) ? O7[8 * (4 + bit) * TW] : 0ull;
                 gray16(base, O7[0], O7[8 * TW], O7[16 * TW], O7[24 * TW], S.U + (vh << 4) * TW + wi, TW);
             }
-            __syncthreads();
+            sweep_sync<NTH, TOFF>();
         }
         const int w0 = wbase + 4 * L.sub;
         const bool interior = wbase >= b + 2 && wbase + TW <= W;
         const int ua = blk0, ub = min(blk1, up_end);
         if (MODE && ua < ub) {
             if (interior)
-                lean_blocks<MODE, true, false, COUNT, KB>(c, S, L, w0, ua, ub, cnt);
+                lean_blocks<MODE, true, false, COUNT, KB, RP>(c, S, L, w0, ua, ub, cnt);
             else
-                lean_blocks<MODE, true, true, COUNT, KB>(c, S, L, w0, ua, ub, cnt);
+                lean_blocks<MODE, true, true, COUNT, KB, RP>(c, S, L, w0, ua, ub, cnt);
         }
         for (int j = max(blk0, up_end); j < min(blk1, plain_blk); ++j)
-            general_block<MODE, COUNT, KB>(c, S, L, w0, j, cnt);
+            general_block<MODE, COUNT, KB, RP>(c, S, L, w0, j, cnt);
         const int ta = max(blk0, plain_blk);
         if (ta < blk1) {
             if (interior)
-                lean_blocks<MODE, false, false, COUNT, KB>(c, S, L, w0, ta, blk1, cnt);
+                lean_blocks<MODE, false, false, COUNT, KB, RP>(c, S, L, w0, ta, blk1, cnt);
             else
-                lean_blocks<MODE, false, true, COUNT, KB>(c, S, L, w0, ta, blk1, cnt);
+                lean_blocks<MODE, false, true, COUNT, KB, RP>(c, S, L, w0, ta, blk1, cnt);
         }
     }
 }
@@ -456,14 +482,14 @@ __device__ __forceinline__ void sweep_body(Cfg &c, SweepSmem &S, unsigned long l
 // One panel's sweep by CTAs cta of ncta. FORM 0: PLS; 1: reduced echelon form; 2: hybrid, the
 // form the pivot search chose for this panel (st->mode), and the set bits of the trailing rows'
 // next panel word are counted into st->pop.
-template <int FORM, int KB>
+template <int FORM, int KB, int NTH = NT, int TOFF = 0>
 __device__ __forceinline__ void sweep_panel16(SweepSmem &S, uint64_t *__restrict__ A, int64_t stride,
                                               const u64 *__restrict__ side_cur, u64 *__restrict__ side_nxt,
                                               const int *__restrict__ perm, const PanelState *__restrict__ st,
                                               uint64_t *__restrict__ out, int64_t ostride, u64 *__restrict__ ups,
                                               int m, int W, int b, int cta, int ncta)
 {
-    const int tid = threadIdx.x;
+    const int tid = (int)threadIdx.x - TOFF;
     Cfg c;
     c.A = A;
     c.stride = stride;
@@ -486,7 +512,7 @@ __device__ __forceinline__ void sweep_panel16(SweepSmem &S, uint64_t *__restrict
     const bool reduced = FORM == 1 || (FORM == 2 && st->mode == 1);
     if (c.kbar == 0 && reduced && b + 1 < W) {
         // the rows above keep their rows; pass their word b + 1 on
-        for (int p = cta * NT + tid; p < c.r; p += ncta * NT)
+        for (int p = cta * NTH + tid; p < c.r; p += ncta * NTH)
             c.ups_nxt[p] = out[(int64_t)p * ostride + b + 1];
     }
     if (c.kbar == 0) {
@@ -495,7 +521,7 @@ __device__ __forceinline__ void sweep_panel16(SweepSmem &S, uint64_t *__restrict
         // any trailing row (none means no later panel has a pivot). Rows above stay as they are.
         const bool check = !st->zero_tail;
         bool nzw = false;
-        for (int p = c.r + cta * NT + tid; p < m; p += ncta * NT) {
+        for (int p = c.r + cta * NTH + tid; p < m; p += ncta * NTH) {
             const int ph = trailing_row(perm, st, c.r, c.nwin, c.nx, p);
             const uint64_t *row = A + (int64_t)ph * stride;
             A[(int64_t)ph * stride + b] = side_cur[ph];
@@ -511,12 +537,12 @@ __device__ __forceinline__ void sweep_panel16(SweepSmem &S, uint64_t *__restrict
                 }
             }
         }
-        if (__syncthreads_or(nzw) && tid == 0)
+        if (sweep_sync_or<NTH, TOFF>(nzw) && tid == 0)
             atomicExch(const_cast<int *>(&st->nz), 1);
     } else if (!reduced) {
-        sweep_body<0, FORM == 2, KB>(c, S, cnt, cta, ncta);
+        sweep_body<0, FORM == 2, KB, NTH, TOFF>(c, S, cnt, cta, ncta);
     } else {
-        sweep_body<1, FORM == 2, 8>(c, S, cnt, cta, ncta);  // the reduced form is built for k = 8
+        sweep_body<1, FORM == 2, 8, NTH, TOFF>(c, S, cnt, cta, ncta);  // the reduced form is built for k = 8
     }
     if (FORM == 2) {
         // the density count for the hybrid's switch

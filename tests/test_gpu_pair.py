@@ -153,3 +153,17 @@ def test_pair_wide_stride_and_caller_workspace(g):
     W = S.words_per_row(n)
     assert (host(D)[:, :W] == R[:, :W]).all()
     assert (host(D)[:, W:] == A[:, W:]).all(), "words past the row's last word were written"
+
+
+def test_pair_random_shapes_kinds_and_grids(g):
+    """Seeded random shapes (1 .. 2600 rows and columns), input kinds and grid sizes, two panels
+    per sweep, against the oracle."""
+    rng = np.random.default_rng(20261204)
+    for i in range(40):
+        m = int(rng.integers(1, 2600))
+        n = int(rng.integers(1, 2600))
+        kind = KINDS[int(rng.integers(len(KINDS)))]
+        grid = int(rng.choice([0, 2, 6, 37, 150]))
+        A = make(kind, m, n, 7000 + i)
+        opts = dict(PAIR, grid_ctas=grid) if grid else PAIR
+        check_pls(g, A, m, n, opts)
