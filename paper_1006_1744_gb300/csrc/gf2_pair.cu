@@ -45,6 +45,7 @@ struct PairSmem {
     u64 Ob[64 * 8], Oc[64 * 8];  // pivot rows of the current tile (Oc: after panel b)
     u64 zpb[64], zpc[64];        // pivot t -> its final row's coordinates (row t of L^-1)
     int prb[64], prc[64];        // physical rows of the pivots
+    int xblk[64];                // blocks holding the positions panel c's search swapped from past its window
 };
 
 struct PairArgs {
@@ -136,7 +137,7 @@ __device__ __forceinline__ void build_tables(u64 *__restrict__ T, const u64 *__r
 struct PairRows {
     int R0, R1, R2;      // panel b's pivots at [R0, R1), panel c's at [R1, R2), trailing rows from R2
     int nwin, nx;        // panel c's window and swaps past it
-    int plain_from;      // positions from here on are perm[p] alone
+    int plain_from;      // positions from here on are perm[p], except panel c's nx swapped ones
 };
 
 // Pipelined sweep of blocks [ja, jb) of trailing rows given by perm alone. Per thread: the
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(NT, 1) k_pair_sweep(PairArgs a)
     R.R2 = R.R1 + sc->kbar;
     R.nwin = sc->nwin;
     R.nx = sc->nx;
-    R.plain_from = R.nx ? INT_MAX : R.R1 + max(sc->kbar, R.nwin);
+    R.plain_from = R.R1 + max(sc->kbar, R.nwin);
     const int kb = sb->kbar, kc = sc->kbar;
     // no pivot in panel c: look for a nonzero word right of it in any trailing row (none means
     // no later panel has a pivot), unless that is known already
@@ -295,9 +296,10 @@ __global__ void __launch_bounds__(NT, 1) k_pair_sweep(PairArgs a)
             S.prc[tid] = tid < kc ? sc->prow[tid] : 0;
             S.zpb[tid] = tid < kb ? sb->zpiv[tid] : 0ull;
             S.zpc[tid] = tid < kc ? sc->zpiv[tid] : 0ull;
+            S.xblk[tid] = tid < R.nx ? (sc->xpos[tid] - R.R0) / RPU : INT_MAX;
         }
         const int nblk = (M + RPU - 1) / RPU;
-        const int plain_blk = R.plain_from == INT_MAX ? nblk : min(nblk, (R.plain_from - R.R0 + RPU - 1) / RPU);
+        const int plain_blk = min(nblk, (R.plain_from - R.R0 + RPU - 1) / RPU);
         // units: (tile, block) in tile-major order; paired: (128-byte line, block), the two CTAs of
         // a pair taking the line's two tiles
         const int half = a.paired ? (int)(blockIdx.x & 1) : 0;
@@ -340,9 +342,17 @@ __global__ void __launch_bounds__(NT, 1) k_pair_sweep(PairArgs a)
             const bool v0 = w0 >= lo && w0 < hi, v1 = w0 + 1 >= lo && w0 + 1 < hi;
             for (int j = blk0; j < min(blk1, plain_blk); ++j)
                 pair_general(a, S, R, sub, rg, odd, w0, v0, v1, j, check, nzw);
-            const int ta = max(blk0, plain_blk);
-            if (ta < blk1)
-                pair_plain(a, S, R, sub, rg, odd, w0, v0, v1, ta, blk1, check, nzw);
+            // runs of plain blocks through the pipeline, each block holding a swapped position alone
+            for (int ja = max(blk0, plain_blk); ja < blk1;) {
+                int jx = blk1;
+                for (int x = 0; x < R.nx; ++x)
+                    jx = S.xblk[x] >= ja && S.xblk[x] < jx ? S.xblk[x] : jx;
+                if (ja < jx)
+                    pair_plain(a, S, R, sub, rg, odd, w0, v0, v1, ja, jx, check, nzw);
+                if (jx < blk1)
+                    pair_general(a, S, R, sub, rg, odd, w0, v0, v1, jx, check, nzw);
+                ja = jx + 1;
+            }
         }
     }
     if (check && __syncthreads_or(nzw) && tid == 0) {

@@ -45,6 +45,7 @@ struct SweepSmem {
     u64 O[64 * TW];       // rows of the tables for the current tile
     u64 map[64];          // zmap of the panel
     int prow[64];         // physical rows of the pivots
+    int xblk[64];         // blocks holding the positions the pivot search swapped from past its window
 };
 
 // row codes: >= 0 trailing row (physical index), -1 none, -2 row above (MODE 1, kept in
@@ -368,14 +369,16 @@ __device__ __forceinline__ void sweep_body(Cfg &c, SweepSmem &S, unsigned long l
     if (q_lo >= q_hi)
         return;
     // blocks [0, up_end) hold only rows above the panel (MODE 1); blocks from plain_blk on hold
-    // only trailing rows that perm alone gives; the blocks between take the general path
+    // trailing rows that perm alone gives, except the blocks holding a position the pivot search
+    // swapped from past its window (xblk); those and the blocks between take the general path
     const int up_end = MODE ? (c.r - c.row0) / RP : 0;
-    const int plain_from = c.nx ? INT_MAX : c.r + max(c.kbar, c.nwin);
-    const int plain_blk = c.nx ? nblk : min(nblk, (plain_from - c.row0 + RP - 1) / RP);
+    const int plain_from = c.r + max(c.kbar, c.nwin);
+    const int plain_blk = min(nblk, (plain_from - c.row0 + RP - 1) / RP);
 
     if (tid < 64) {
         S.map[tid] = st->zmap[tid];
         S.prow[tid] = tid < c.kbar ? st->prow[tid] : 0;
+        S.xblk[tid] = tid < c.nx ? (st->xpos[tid] - c.row0) / RP : INT_MAX;
     }
     sweep_sync<NTH, TOFF>();
     if (tid < 8 * 16) {
@@ -468,12 +471,20 @@ __device__ __forceinline__ void sweep_body(Cfg &c, SweepSmem &S, unsigned long l
         }
         for (int j = max(blk0, up_end); j < min(blk1, plain_blk); ++j)
             general_block<MODE, COUNT, KB, RP>(c, S, L, w0, j, cnt);
-        const int ta = max(blk0, plain_blk);
-        if (ta < blk1) {
-            if (interior)
-                lean_blocks<MODE, false, false, COUNT, KB, RP>(c, S, L, w0, ta, blk1, cnt);
-            else
-                lean_blocks<MODE, false, true, COUNT, KB, RP>(c, S, L, w0, ta, blk1, cnt);
+        // runs of plain blocks through the pipeline, each block holding a swapped position alone
+        for (int ja = max(blk0, plain_blk); ja < blk1;) {
+            int jx = blk1;
+            for (int x = 0; x < c.nx; ++x)
+                jx = S.xblk[x] >= ja && S.xblk[x] < jx ? S.xblk[x] : jx;
+            if (ja < jx) {
+                if (interior)
+                    lean_blocks<MODE, false, false, COUNT, KB, RP>(c, S, L, w0, ja, jx, cnt);
+                else
+                    lean_blocks<MODE, false, true, COUNT, KB, RP>(c, S, L, w0, ja, jx, cnt);
+            }
+            if (jx < blk1)
+                general_block<MODE, COUNT, KB, RP>(c, S, L, w0, jx, cnt);
+            ja = jx + 1;
         }
     }
 }
