@@ -609,6 +609,34 @@ def test_pls_batched_persistent_teams(g):
             assert (host(ds[i])[:, :W] == R[:, :W]).all(), (mode, i)
 
 
+def test_pls_batched_persistent_many_medium_members(g):
+    """160 members of 2048 to 2600 rows, enough that the persistent plan forms no team: each
+    member is eliminated by one CTA from the work queue (the pivot search of panel b + 1 beside
+    the sweep of panel b). Every input kind, word counts from one up, pivots past the window and
+    rank deficiency, against the oracle."""
+    rng = np.random.default_rng(61)
+    kinds = ["dense", "sparse05", "sparse01", "echelon", "lowrank", "deep", "dup", "zero", "identity", "ones"]
+    hosts = []
+    for i in range(160):
+        m = int(rng.integers(2048, 2600))
+        n = int(rng.choice([1, 63, 64, 65, 128, 129, 192, 256, 300, 449, 640, 700]))
+        hosts.append((make(kinds[i % len(kinds)], m, n, 6100 + i), m, n))
+    team_of, team_size, member_team = g.batch_plan([(m, n) for (_, m, n) in hosts], 152)
+    assert (np.asarray(member_team) < 0).all(), "a member went to a team"
+    want = [oracle.pls(A, m, n) for (A, m, n) in hosts]
+    ds = [dev(A) for (A, _, _) in hosts]
+    Ps, Qs, ranks = g.pls_batched(ds, [n for (_, _, n) in hosts], opts={"batch_mode": g.BATCH_PERSISTENT})
+    torch.cuda.synchronize()
+    assert g.sync_status() == 0
+    rk = ranks.cpu().numpy()
+    for i, (A, m, n) in enumerate(hosts):
+        R, P, Q, r = want[i]
+        assert rk[i] == r, (i, m, n)
+        assert (Ps[i].cpu().numpy()[:m] == P[:m]).all() and (Qs[i].cpu().numpy()[:n] == Q[:n]).all(), (i, m, n)
+        W = S.words_per_row(n)
+        assert (host(ds[i])[:, :W] == R[:, :W]).all(), (i, m, n)
+
+
 def test_autotune_choices_are_exact_and_cached(g):
     """The autotuner only picks among settings that change no result: PLS with its
     choice matches the oracle, and a second call returns the cached choice."""
