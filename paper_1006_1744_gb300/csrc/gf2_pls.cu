@@ -1188,6 +1188,30 @@ k_sweep(uint64_t *__restrict__ A, int64_t stride, const u64 *__restrict__ side_c
 // (all words for p >= r, the words left of the pivot's panel for p < r),
 // identity fill of P and Q beyond the rank, rank.
 // ---------------------------------------------------------------------------
+// Words [0, nw) of one row from src to dst by the 32 lanes of a warp, 16 bytes per access and up
+// to four accesses of a lane in flight. Both rows start on a 16-byte boundary: matrices and the
+// workspace are 128-byte aligned with strides of whole 128-byte lines, and the recursive PLS's
+// column views start on an even word (its splits fall on multiples of 128 columns).
+__device__ __forceinline__ void copy_words(uint64_t *__restrict__ dst, const uint64_t *__restrict__ src, int nw,
+                                           int lane)
+{
+    const int n2 = nw >> 1;  // whole 16-byte pairs
+    const ulonglong2 *__restrict__ s2 = reinterpret_cast<const ulonglong2 *>(src);
+    ulonglong2 *__restrict__ d2 = reinterpret_cast<ulonglong2 *>(dst);
+    int i = lane;
+    for (; i + 96 < n2; i += 128) {
+        const ulonglong2 a = s2[i], b = s2[i + 32], c = s2[i + 64], e = s2[i + 96];
+        d2[i] = a;
+        d2[i + 32] = b;
+        d2[i + 64] = c;
+        d2[i + 96] = e;
+    }
+    for (; i < n2; i += 32)
+        d2[i] = s2[i];
+    if ((nw & 1) && lane == 0)
+        dst[nw - 1] = src[nw - 1];
+}
+
 __device__ __forceinline__ void gather_rows(const uint64_t *__restrict__ A, int64_t stride,
                                             const int *__restrict__ perm, const PanelState *__restrict__ st,
                                             int64_t *__restrict__ P, int64_t *__restrict__ Q,
@@ -1202,10 +1226,7 @@ __device__ __forceinline__ void gather_rows(const uint64_t *__restrict__ A, int6
         for (int p = wid; p < m; p += warps) {
             const int ph = perm[p];
             const int wend = p < r ? (int)(Q[p] >> 6) : W;
-            const uint64_t *src = A + (int64_t)ph * stride;
-            uint64_t *dst = out + (int64_t)p * ostride;
-            for (int w = lane; w < wend; w += 32)
-                dst[w] = src[w];
+            copy_words(out + (int64_t)p * ostride, A + (int64_t)ph * stride, wend, lane);
         }
     }
     const int g = cta * blockDim.x + threadIdx.x;
@@ -1438,12 +1459,8 @@ __global__ void k_copyback_b(const gf2::ElimDesc *__restrict__ D)
     const gf2::ElimDesc &d = D[blockIdx.y];
     const int warps = gridDim.x * (blockDim.x >> 5);
     const int lane = threadIdx.x & 31;
-    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < d.m; i += warps) {
-        const uint64_t *src = d.out + (int64_t)i * d.ostride;
-        uint64_t *dst = d.A + (int64_t)i * d.stride;
-        for (int w = lane; w < d.W; w += 32)
-            dst[w] = src[w];
-    }
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < d.m; i += warps)
+        copy_words(d.A + (int64_t)i * d.stride, d.out + (int64_t)i * d.ostride, d.W, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -1574,12 +1591,8 @@ __device__ bool team_eliminate(SweepSmem &S, const gf2::ElimDesc &d, int tr, int
     if (!team_barrier(bar, target, G, pl))
         return false;
     const int lane = tid & 31;
-    for (int i = (tr * NT + tid) >> 5; i < m; i += gs >> 5) {
-        const uint64_t *src = d.out + (int64_t)i * d.ostride;
-        uint64_t *dst = d.A + (int64_t)i * d.stride;
-        for (int w = lane; w < W; w += 32)
-            dst[w] = src[w];
-    }
+    for (int i = (tr * NT + tid) >> 5; i < m; i += gs >> 5)
+        copy_words(d.A + (int64_t)i * d.stride, d.out + (int64_t)i * d.ostride, W, lane);
     return team_barrier(bar, target, G, pl);
 }
 
