@@ -447,9 +447,6 @@ __device__ __forceinline__ int pair_row(const int *__restrict__ perm, const Pane
     return perm[p];
 }
 
-// The work is ordered so that everything before the marked point reads only this pair's pivot
-// search results and the words b, b + 1 that the previous front wrote; the words b + 2, b + 3 of
-// the rows (the previous sweep's) and every write come after it.
 __global__ void __launch_bounds__(NT, 1)
 k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, const PanelState *__restrict__ sb,
              const PanelState *__restrict__ sc, u64 *__restrict__ zb, u64 *__restrict__ zc,
@@ -477,7 +474,8 @@ k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, c
     // a CTA past the last row only takes its share of the row-order update below
     const bool rows = R0 + (int)blockIdx.x < m;
     const bool pivots = rows && (kb > 0 || kc > 0);
-    // ---- before the wait: the maps of words b and b + 1 ----
+    // every word this launch reads was written before it started (the previous pair's front
+    // and sweep precede it on the stream): one round of loads, then the tables in six phases
     int p = R0 + g, ph = -1;
     u64 w0 = 0, w1 = 0, w2 = 0, w3 = 0;
     if (pivots && p >= R1 && p < m) {
@@ -485,22 +483,33 @@ k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, c
         const ulonglong2 lo = *reinterpret_cast<const ulonglong2 *>(Fc + 4 * (int64_t)ph);
         w0 = lo.x;
         w1 = lo.y;
+        if (p >= R2) {
+            const ulonglong2 hi = *reinterpret_cast<const ulonglong2 *>(Fc + 4 * (int64_t)ph + 2);
+            w2 = hi.x;
+            w3 = hi.y;
+        }
     }
     if (pivots) {
         if (tid < 64) {
+            // the pivot rows' words b .. b + 3 (panel c's as they were before panel b)
             const int t = tid;
             S.prb[t] = t < kb ? sb->prow[t] : 0;
             S.prc[t] = t < kc ? sc->prow[t] : 0;
             S.Xb[t] = t < kb ? sb->newblk[t] & sb->J & lowmask(sb->pcol[t] + 1) : 0ull;
-            S.Ob[0][t] = t < kb && has1 ? Fc[4 * (int64_t)S.prb[t] + 1] : 0ull;
             S.Xc[t] = t < kc ? sc->newblk[t] & sc->J & lowmask(sc->pcol[t] + 1) : 0ull;
-            S.Oc[0][t] = t < kc ? Fc[4 * (int64_t)S.prc[t]] : 0ull;
+            const u64 *fb = Fc + 4 * (int64_t)S.prb[t], *fc = Fc + 4 * (int64_t)S.prc[t];
+            S.Ob[0][t] = t < kb && has1 ? fb[1] : 0ull;
+            S.Ob[1][t] = t < kb && has2 ? fb[2] : 0ull;
+            S.Ob[2][t] = t < kb && has3 ? fb[3] : 0ull;
+            S.Oc[0][t] = t < kc ? fc[0] : 0ull;
+            S.Oc[1][t] = t < kc && has2 ? fc[2] : 0ull;
+            S.Oc[2][t] = t < kc && has3 ? fc[3] : 0ull;
         }
         __syncthreads();
-        for (int e = tid; e < 4 * 256; e += NT) {
-            const int k = e >> 8;  // Xb, Ob0, zmb, Xc
-            const int slot = k == 0 ? N_XB : k == 1 ? N_OB0 : k == 2 ? N_ZMB : N_XC;
-            const u64 *src = k == 0 ? S.Xb : k == 1 ? S.Ob[0] : k == 2 ? S.zmb : S.Xc;
+        for (int e = tid; e < 6 * 256; e += NT) {
+            const int k = e >> 8;  // Xb, Ob0, zmb, Xc, Ob1, Ob2
+            const int slot = k == 0 ? N_XB : k == 1 ? N_OB0 : k == 2 ? N_ZMB : k == 3 ? N_XC : k == 4 ? N_OB1 : N_OB2;
+            const u64 *src = k == 0 ? S.Xb : k == 1 ? S.Ob[0] : k == 2 ? S.zmb : k == 3 ? S.Xc : S.Ob[k - 3];
             build_nib(S.nib[slot], src, e & 255);
         }
         __syncthreads();
@@ -515,15 +524,36 @@ k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, c
             const u64 zm = S.zmc[i];
             S.img[M_ZC + mp][i] = mp == 0 ? zm : select_sum(zm, S.nib[N_XC]);
         } else if (tid < 6 * 64) {
-            // panel c's pivot rows: their coordinates over panel b's pivot rows
+            // panel c's pivot rows: their coordinates over panel b's pivot rows, and their words
+            // b + 2, b + 3 after panel b
             const int t = tid - 5 * 64;
-            S.ztc[t] = t < kc ? select_sum(S.Oc[0][t], S.nib[N_ZMB]) : 0ull;
+            const u64 z = t < kc ? select_sum(S.Oc[0][t], S.nib[N_ZMB]) : 0ull;
+            S.ztc[t] = z;
+            if (t < kc) {
+                S.Oc[1][t] ^= select_sum(z, S.nib[N_OB1]);
+                S.Oc[2][t] ^= select_sum(z, S.nib[N_OB2]);
+            }
+        } else {
+            // panel b's contributions to words b + 2, b + 3
+            const int mp = (tid >> 6) - 6, i = tid & 63;
+            S.img[M_E2B + mp][i] = select_sum(S.zmb[i], S.nib[N_OB1 + mp]);
         }
         __syncthreads();
-        build_bytetabs(S, M_ZB, M_CB + 1);
+        build_bytetabs(S, M_ZB, M_E3B + 1);
         build_bytetabs(S, M_ZC, M_XC + 1);
+        for (int e = tid; e < 2 * 256; e += NT)
+            build_nib(S.nib[N_OC1 + (e >> 8)], S.Oc[1 + (e >> 8)], e & 255);
+        __syncthreads();
+        if (tid < 2 * 64) {
+            // panel c's contributions to words b + 2, b + 3
+            const int mp = tid >> 6, i = tid & 63;
+            S.img[M_E2C + mp][i] = select_sum(S.zmc[i], S.nib[N_OC1 + mp]);
+        }
+        __syncthreads();
+        build_bytetabs(S, M_E2C, M_E3C + 1);
+        __syncthreads();
     }
-    // ---- then: panel b's row order, the words b + 2, b + 3 and every write ----
+    // panel b's row order into perm (the rows below read it through sb)
     if (sc) {
         for (int i = g; i < nwb; i += gs)
             perm[R0 + i] = sb->wperm[i];
@@ -550,46 +580,6 @@ k_pair_front(uint64_t *__restrict__ A, int64_t stride, int *__restrict__ perm, c
         }
         return;
     }
-    if (ph >= 0 && p >= R2) {
-        const ulonglong2 hi = *reinterpret_cast<const ulonglong2 *>(Fc + 4 * (int64_t)ph + 2);
-        w2 = hi.x;
-        w3 = hi.y;
-    }
-    if (tid < 64) {
-        const int t = tid;
-        S.Ob[1][t] = t < kb && has2 ? Fc[4 * (int64_t)S.prb[t] + 2] : 0ull;
-        S.Ob[2][t] = t < kb && has3 ? Fc[4 * (int64_t)S.prb[t] + 3] : 0ull;
-        S.Oc[1][t] = t < kc && has2 ? Fc[4 * (int64_t)S.prc[t] + 2] : 0ull;
-        S.Oc[2][t] = t < kc && has3 ? Fc[4 * (int64_t)S.prc[t] + 3] : 0ull;
-    }
-    __syncthreads();
-    for (int e = tid; e < 2 * 256; e += NT)
-        build_nib(S.nib[N_OB1 + (e >> 8)], S.Ob[1 + (e >> 8)], e & 255);
-    __syncthreads();
-    if (tid < 2 * 64) {
-        // panel b's contributions to words b + 2, b + 3
-        const int mp = tid >> 6, i = tid & 63;
-        S.img[M_E2B + mp][i] = select_sum(S.zmb[i], S.nib[N_OB1 + mp]);
-    } else if (tid < 3 * 64) {
-        // panel c's pivot rows at words b + 2, b + 3 after panel b
-        const int t = tid - 2 * 64;
-        if (t < kc) {
-            S.Oc[1][t] ^= select_sum(S.ztc[t], S.nib[N_OB1]);
-            S.Oc[2][t] ^= select_sum(S.ztc[t], S.nib[N_OB2]);
-        }
-    }
-    __syncthreads();
-    for (int e = tid; e < 2 * 256; e += NT)
-        build_nib(S.nib[N_OC1 + (e >> 8)], S.Oc[1 + (e >> 8)], e & 255);
-    __syncthreads();
-    if (tid < 2 * 64) {
-        const int mp = tid >> 6, i = tid & 63;
-        S.img[M_E2C + mp][i] = select_sum(S.zmc[i], S.nib[N_OC1 + mp]);
-    }
-    __syncthreads();
-    build_bytetabs(S, M_E2B, M_E3B + 1);
-    build_bytetabs(S, M_E2C, M_E3C + 1);
-    __syncthreads();
     for (; p < m; p += gs) {
         if (ph < 0 && p >= R1) {
             // a later row of this thread (more rows than threads)
