@@ -775,6 +775,11 @@ def run_headline(args):
     bytes_per_launch = sweep_bytes / max(sweep_n, 1)
     prof_name = f"k_pair_sweep_{n}" if pair else f"k_sweep16_{n}"
     traffic_ratio = traffic_from_profiles(prof_name)
+    # a capture of an earlier build of the kernel gives no traffic for this one
+    stale = profile_value(prof_name, "captured_kernel_current") == 0
+    ratio_at_capture = traffic_ratio
+    if stale:
+        traffic_ratio = None
     kname = ("k_pair_sweep (table sweep of two panels: MakeTable1 + AddRowsFromTable over 128 pivot columns)"
              if pair else "k_sweep16 (table sweep: MakeTable1 + AddRowsFromTable)")
     roofline = {"kernel": kname, "bound": "hbm",
@@ -782,13 +787,17 @@ def run_headline(args):
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst)" if peak_kind == "measured"
                 else peak_kind,
                 "traffic": traffic_ratio * bytes_per_launch if traffic_ratio else None,
-                "traffic_note": f"DRAM bytes / algorithmic bytes of one captured launch (profiles/{prof_name}.md) "
-                                "x the average launch's algorithmic bytes" if traffic_ratio else "no capture",
+                "traffic_note": (f"DRAM bytes / algorithmic bytes of one captured launch (profiles/{prof_name}.md) "
+                                 "x the average launch's algorithmic bytes" if traffic_ratio else
+                                 f"null: the kernel changed after its capture (profiles/{prof_name}.md); that "
+                                 f"earlier build's DRAM / algorithmic bytes: {ratio_at_capture}" if stale
+                                 else "no capture"),
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_us": sweep_ms * 1e3 / max(sweep_n, 1),
                 "binding_unit": {"unit": "L1/shared-memory data port (l1tex throughput, pct of peak)",
                                  "frac": profile_value(prof_name, "l1_port_frac"),
-                                 "source": f"profiles/{prof_name}.md (one captured launch)"}
+                                 "source": f"profiles/{prof_name}.md (one captured launch"
+                                           + (", an earlier build of the kernel)" if stale else ")")}
                 if pair else None,
                 "note": ("bytes per sweep of panels b, b + 1 = (m - r_b)(W - b - 4) x 16 (read + write of the "
                          "trailing words right of the front's four); half the DRAM traffic per panel of one "
